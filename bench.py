@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Throughput of the batched ECC-island LLG path (island-ns/s).
+
+Workload: 4096 jittered ECC islands sharing one ~1500-node P1 cylinder mesh
+(8 nm, soft 3 nm on hard 7 nm), synthetic 64x64x16 head-field map at 1 nm,
+head moving at 20 m/s, alpha 0.1, output interval 0.1 ps split into the
+stable number of Heun steps.  One bench step = one output interval for every
+island (one CUDA-graph replay: per Heun step two demag GEMMs and the two Heun
+stage kernels).  value = islands * simulated ns / device seconds, all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp32|bf16]
+  python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "island-ns/s batched LLG (mixed vs plain, same outcomes); surrogate evals/s"
+UNIT = "island-ns/s"
+DT_PS = 0.1
+B_ISLANDS = 4096
+SM_FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def workload(seed: int = 1):
+    from paper_1603_09493_gb300 import synth
+    mesh = synth.census_island_mesh(seed=seed)
+    mats = synth.ecc_materials()
+    hm = synth.synthetic_head_map()
+    p = synth.RunParams(dt_ps=DT_PS, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=-10.0, use_map=True,
+                        t_end_ps=DT_PS)
+    return mesh, mats, hm, p
+
+
+def config_dict(mesh, k, precision, B, n_gpus):
+    return {"workload": f"census batch: {B} jittered ECC islands per GPU on one {mesh.n_nodes}-node P1 cylinder "
+                        "mesh (8 nm, soft 3 nm / hard 7 nm), 64x64x16 head map at 1 nm, 20 m/s, 0.1 ps intervals",
+            "islands_per_gpu": B, "nodes": mesh.n_nodes, "heun_steps_per_interval": k, "dt_ps": DT_PS,
+            "demag_precision": precision, "parallelism": f"islands sharded over {n_gpus} GPU(s), no collective",
+            "l2": "per-step working set (state, stages, demag operand and field, BF16/FP32 operator) > 129 MB L2"}
+
+
+def sample_clocks_start():
+    try:
+        f = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                 else os.devnull, "w")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"],
+                                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        return proc, f
+    except Exception:
+        return None, None
+
+
+def sample_clocks_stop(proc, f, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except Exception:
+        proc.kill()
+        return None
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = max(mx, float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if f is not None:
+        f.write(out)
+        f.close()
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def run_oracle_sample(islands, n_intervals, k, mesh, mats, hm, p):
+    """Time the FP64 oracle on a bounded sample; returns seconds."""
+    from oracle import fem, llg
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    pp = type(p)(**{**p.__dict__})
+    pp.substeps = k
+    pp.t_end_ps = pp.t0_ps + n_intervals * pp.dt_ps
+    b = llg.Batch(ops, islands, pp, head_map=hm)
+    t = time.perf_counter()
+    b.run()
+    return time.perf_counter() - t
+
+
+def cpu_baseline(mesh, mats, hm, p, k, target_s=15.0):
+    from paper_1603_09493_gb300 import synth
+    isl = synth.jittered_islands(16, seed=1)
+    t1 = run_oracle_sample(isl, 1, k, mesh, mats, hm, p)
+    nint = int(max(1, min(40, round(target_s / max(t1, 1e-3)))))
+    t = run_oracle_sample(isl, nint, k, mesh, mats, hm, p)
+    value = len(isl) * nint * DT_PS * 1e-3 / t
+    return {"value": value, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"{len(isl)} islands x {nint} intervals ({nint * k} Heun steps) of the same workload, "
+                      f"numpy FP64, {t:.1f} s"}
+
+
+def stable_k(ctx, mid, hm, isl, p):
+    from paper_1603_09493_gb300 import api
+    return api.stable_substeps(api.field_bound(ctx, mid, isl, p, hm), p.dt_ps, p.alpha)
+
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1603_09493_gb300 import synth
+    from oracle import fem, llg
+    mesh, mats, hm, p = workload()
+    isl = synth.jittered_islands(8, seed=1)
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    pp = type(p)(**{**p.__dict__})
+    bt = llg.Batch(ops, isl, pp, head_map=hm)
+    k = llg.stable_substeps(bt)
+    pp.substeps = k
+    pp.t_end_ps = DT_PS
+    for _ in range(args.warmup):
+        bt.run()
+    t = time.perf_counter()
+    m = None
+    for s in range(args.steps):
+        pp.t0_ps = s * DT_PS
+        pp.t_end_ps = (s + 1) * DT_PS
+        r = bt.run(m)
+        m = r["m"]
+    el = time.perf_counter() - t
+    value = len(isl) * args.steps * DT_PS * 1e-3 / el
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(mesh, k, "fp64 (oracle)", len(isl), 1), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"{len(isl)} islands per step, one 0.1 ps interval ({k} Heun steps) each"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main(args):
+    if args.impl == "reference":
+        return main_reference(args)
+    import torch
+    from paper_1603_09493_gb300 import _lib as L
+    from paper_1603_09493_gb300 import api, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if not os.path.exists(L.LIB_PATH):
+        from paper_1603_09493_gb300 import build
+        build.build()
+    prec = {"bf16x3": L.PREC_BF16X3, "fp32": L.PREC_FP32, "bf16": L.PREC_BF16}[args.precision]
+    mesh, mats, hm, p = workload()
+    B = args.islands
+    isl = synth.jittered_islands(B, seed=1, first_index=rank * B)
+    stream = torch.cuda.Stream()
+    ctx = api.Context(local if world > 1 else 0, stream=stream)
+    mid = ctx.mesh_upload(mesh, mats)
+    isl.mesh_id[:] = mid
+    hid = ctx.headmap_upload(hm)
+    k = stable_k(ctx, mid, hm, isl, p)
+    p.substeps = k
+    bt = ctx.batch(isl, p, precision=prec, map_id=hid)
+    for _ in range(max(args.warmup, 1)):
+        bt.advance(1)
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    proc, cf = sample_clocks_start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bt.advance(1)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sample_clocks_stop(proc, cf, local)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    out = bt.read()
+    ok = bool(np.all(out["status"] == 0))
+    value = world * B * args.steps * DT_PS * 1e-3 / (ms * 1e-3)
+    # kernel durations (events on the launching stream, outside the graph)
+    kt = bt.kernel_times(reps=max(4, min(2 * k, 40)))
+    bt.destroy()
+    n = mesh.n_nodes
+    K3 = 3 * n
+    products = {L.PREC_BF16X3: 3, L.PREC_BF16: 1, L.PREC_FP32: 1}[prec]
+    gemm_flops = products * 2.0 * B * K3 * K3
+    pk = peaks()
+    if prec == L.PREC_FP32:
+        roof = {"bound": "alu", "achieved": gemm_flops / (kt["gemm_ms"] * 1e-3) / 1e12,
+                "peak": SM_FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"}
+    else:
+        peak = pk["bf16_tflops_sustained"] if pk else 1700.0
+        roof = {"bound": "tensor", "achieved": gemm_flops / (kt["gemm_ms"] * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained" if pk else "fallback"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "demag GEMM"
+    # step kernels: algorithmic HBM bytes (stage 1: 60 n, stage 2: 72 n per island)
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
+    ab = 2 if prec != L.PREC_FP32 else 1
+    s1_bytes = B * n * (12 + 12 + 12 + 12 + 6 * ab)
+    s2_bytes = B * n * (12 * 4 + 12 + 6 * ab)
+    roof_steps = {"bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
+                  "stage1_achieved": s1_bytes / (kt["stage1_ms"] * 1e-3) / 1e9,
+                  "stage2_achieved": s2_bytes / (kt["stage2_ms"] * 1e-3) / 1e9}
+    roof_steps["stage1_frac"] = roof_steps["stage1_achieved"] / hbm_peak
+    roof_steps["stage2_frac"] = roof_steps["stage2_achieved"] / hbm_peak
+
+    # end to end through the one-call public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        isl_arr = api.island_array(isl)
+        pin = torch.empty(isl_arr.nbytes, dtype=torch.uint8).pin_memory()
+        pin.numpy()[:] = isl_arr.view(np.uint8)
+        m_h = torch.empty((B, 3, n), dtype=torch.float32).pin_memory()
+        sw_h = torch.empty(B, dtype=torch.uint8).pin_memory()
+        ts_h = torch.empty(B, dtype=torch.float32).pin_memory()
+        st_h = torch.empty(B, dtype=torch.int32).pin_memory()
+        q = api.run_params(p, prec, hid)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.check(ctx.lib.bpm_run_batch(ctx.h, L.ptr(pin), B, __import__("ctypes").byref(q), args.steps,
+                                      L.ptr(m_h), n, L.ptr(sw_h), L.ptr(ts_h), L.ptr(st_h)))
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * B * args.steps * DT_PS * 1e-3 / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(isl_arr.nbytes) / args.steps,
+               "d2h_bytes_per_step": int(m_h.numel() * 4 + B * 9) / args.steps,
+               "note": "one bpm_run_batch call per run of K intervals: batch setup, graph capture, island-table "
+                       "H2D, K intervals, m_final/flags D2H"}
+    ctx.close()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16x3": "bf16x3+f32", "fp32": "f32", "bf16": "bf16+f32"}[args.precision],
+            "data": "synthetic", "config": config_dict(mesh, k, args.precision, B, world),
+            "e2e": e2e, "gpu_launches": args.steps * (4 * k + 1), "roofline": roof, "roofline_step_kernels": roof_steps,
+            "kernel_ms": kt, "clocks": clocks, "status_ok": ok}
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(mesh, mats, hm, p, k)
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "bf16"])
+    ap.add_argument("--islands", type=int, default=B_ISLANDS)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    sys.exit(main(ap.parse_args()))

@@ -1,0 +1,219 @@
+/*
+ * bpm.h -- C ABI of the GB300 batched ECC-island LLG library (libbpmllg.so).
+ *
+ * The library integrates the Landau-Lifshitz-Gilbert equation at 0 K for a
+ * batch of exchange-coupled-composite bit-patterned islands under a moving
+ * write-head field (the recording simulations of Sec. II.A and II.C of
+ * Kovacs et al., "Numerical optimization of writer and media for bit
+ * patterned magnetic recording", J. Appl. Phys. 120, 013902 (2016)), and
+ * trains/evaluates a small MLP surrogate on the outcomes.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: BPM_OK (0) or a negative BPM_ERR_* code; the message of
+ *     the last failure on the calling thread is bpm_last_error().
+ *   - Ownership: the caller owns every pointer it passes; the library copies
+ *     what it keeps.  Handles (bpm_ctx, bpm_batch, ids) are owned by the
+ *     library and released by the matching destroy call.
+ *   - Device pointers (arguments documented "device") must be device memory
+ *     of the context's GPU; all work is ordered on the context's stream.
+ *     Entry points taking host pointers synchronise the stream before return.
+ *   - Units: nm, ps, tesla (mu0*H), A/m, J/m^3, J/m.
+ *   - Magnetisation arrays are component-planar per island: m[b][c][i] at
+ *     float offset (b*3 + c)*ld + i, c = x,y,z, i < n_nodes <= ld.
+ *   - Initial state m = +z; "switched" means the volume-averaged m_z has
+ *     reached <= 0 (writing targets -z).
+ *   - Nothing blocks on the GPU without a bound: device-side waits give up
+ *     after a fixed number of polls and report BPM_ERR_TIMEOUT.
+ */
+#ifndef BPM_H
+#define BPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define BPM_OK             0
+#define BPM_ERR_ARG       (-1)   /* invalid argument (null, size, id, layout) */
+#define BPM_ERR_CUDA      (-2)   /* a CUDA runtime/driver call failed */
+#define BPM_ERR_OOM       (-3)   /* device allocation failed */
+#define BPM_ERR_TIMEOUT   (-4)   /* a bounded device-side wait gave up */
+#define BPM_ERR_NONFINITE (-5)   /* a solve produced NaN/Inf */
+#define BPM_ERR_UNSTABLE  (-6)   /* an iterative solve did not converge */
+#define BPM_ERR_STATE     (-7)   /* call not valid in the object's state */
+
+/* ---- effective-field terms (term_mask bits) ---- */
+#define BPM_TERM_EXCHANGE   1u   /* lumped P1 exchange */
+#define BPM_TERM_ANISOTROPY 2u   /* uniaxial anisotropy */
+#define BPM_TERM_DEMAG      4u   /* Fredkin-Koehler demagnetising field */
+#define BPM_TERM_HEAD       8u   /* moving head-field map */
+#define BPM_TERM_UNIFORM   16u   /* uniform ramped field + per-island constant field */
+#define BPM_TERM_ALL       31u
+
+/* ---- demag GEMM precision ---- */
+#define BPM_PREC_FP32    0  /* FP32 operands, FP32 CUDA-core GEMM (the plain form) */
+#define BPM_PREC_BF16X3  1  /* BF16 hi+lo split of both operands, three tcgen05 products
+                               (hi*hi + lo*hi + hi*lo), FP32 accumulate in TMEM */
+#define BPM_PREC_BF16    2  /* one BF16 tcgen05 product (hi*hi), FP32 accumulate */
+#define BPM_PREC_BF16X3_REF 3  /* the BF16X3 products evaluated on CUDA cores: a slow
+                                  reference for validating the tensor-core kernel */
+
+/* ---- per-island status bits ---- */
+#define BPM_ISLAND_NONFINITE 1  /* the island's state became NaN/Inf */
+
+/* ---- operators that bpm_mesh_get_operator can export ---- */
+#define BPM_OP_EXCHANGE_F32  0  /* [n][n] float: S with B_ex = -S m (tesla), as used by the kernels */
+#define BPM_OP_DEMAG_F64     1  /* [3n][3n] double: N with H = -N M, index c*n+i (needs BPM_MESH_KEEP_F64) */
+#define BPM_OP_DEMAG_F32     2  /* [3n][3n] float: -mu0*1e6*N, the FP32 GEMM operand (tesla per MA/m) */
+#define BPM_OP_VOLUMES_F64   3  /* [n] double: lumped nodal volumes V_i (nm^3) */
+#define BPM_OP_NODAL_MS_F64  4  /* [n] double: nodal Ms_i (A/m) */
+#define BPM_OP_NODAL_KU_F64  5  /* [n] double: nodal Ku_i (J/m^3) */
+
+/* ---- mesh upload flags ---- */
+#define BPM_MESH_KEEP_F64  1u   /* keep the FP64 demag matrix on the device (for export) */
+
+typedef struct bpm_ctx bpm_ctx;
+typedef struct bpm_batch bpm_batch;
+
+/* Material of one mesh region (Sec. II.B, Fig. 3; Table I row A_ex,int). */
+typedef struct {
+    double Ms_A_per_m;   /* saturation magnetisation */
+    double Ku_J_per_m3;  /* uniaxial anisotropy constant */
+    double A_J_per_m;    /* exchange stiffness */
+} bpm_region_mat;
+
+/* One island of a batch (44 bytes, 4-byte aligned). */
+typedef struct {
+    int32_t mesh_id;     /* mesh returned by bpm_mesh_upload */
+    float   Ms_scale;    /* Ms multiplier (jitter) */
+    float   Ku_scale;    /* Ku multiplier (jitter) */
+    float   u[3];        /* easy axis, unit vector */
+    float   pos_nm[2];   /* island centre in the media frame (x down-track, y cross-track) */
+    float   Hext_T[3];   /* constant field on this island (the H_ext of Sec. II.C), tesla */
+} bpm_island;
+
+/* Run parameters shared by all islands of a batch. */
+typedef struct {
+    double   dt_ps;       /* output interval (0.1 ps in the workloads) */
+    int32_t  substeps;    /* Heun steps per output interval, >= 1 (step h = dt/substeps) */
+    int32_t  precision;   /* BPM_PREC_* */
+    double   t0_ps;       /* start time */
+    double   alpha;       /* Gilbert damping */
+    double   rise_ps;     /* linear rise of head and uniform field, ramp = min(1, t/rise); <= 0: none */
+    double   v_m_per_s;   /* head velocity along +x */
+    double   x0_nm;       /* head position at t = 0 */
+    int32_t  map_id;      /* head map from bpm_headmap_upload, or -1 */
+    uint32_t term_mask;   /* BPM_TERM_* */
+    float    uniform_T[3];/* uniform field, ramped */
+    float    pad_;
+} bpm_run_params;
+
+/* Facts about an uploaded mesh. */
+typedef struct {
+    int32_t n_nodes, n_pad, n_tets, n_boundary;
+    int32_t nnz;                 /* exchange CSR entries including the diagonal */
+    int32_t cg_iters_neumann, cg_iters_dirichlet, pad_;
+    double  volume_nm3;
+    double  exchange_lambda_max_T;  /* largest eigenvalue of S (nominal Ms), power iteration */
+    double  field_bound_T;          /* lambda_max + max anisotropy field + mu0*max Ms */
+    double  cg_residual_neumann, cg_residual_dirichlet;
+} bpm_mesh_info;
+
+/* ---------------------------------------------------------------------- */
+/* Context                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+ * order all work on, or NULL for a stream the library creates.  Returns
+ * BPM_ERR_CUDA if the device is absent or not sm_103. */
+int  bpm_create(bpm_ctx** out, int device, void* cuda_stream);
+void bpm_destroy(bpm_ctx* ctx);
+/* Message of the last failure on the calling thread ("" if none). */
+const char* bpm_last_error(void);
+/* Library version string. */
+const char* bpm_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* Mesh and operators (Sec. II.A hybrid FEM/BEM, Fig. 3 media)             */
+/* ---------------------------------------------------------------------- */
+
+/* Upload one P1 tetrahedral island mesh and assemble its operators on the GPU
+ * in FP64: lumped volumes, nodal Ms/Ku, the exchange operator (stored FP32,
+ * difference form, sliced-ELL), and the dense Fredkin-Koehler demag matrix
+ * (Neumann and Dirichlet Poisson solves by batched preconditioned CG, the
+ * Lindholm double-layer matrix), stored as FP32 and as a BF16 hi/lo pair.
+ *   xyz_nm     [n_nodes][3] host, node positions
+ *   tets       [n_tets][4]  host, node indices, any orientation
+ *   tet_region [n_tets]     host, index into mats
+ *   mats       [n_regions]  host
+ * Errors: BPM_ERR_ARG (bad index, degenerate tet, n_nodes > 16384),
+ *         BPM_ERR_UNSTABLE (CG not converged), BPM_ERR_OOM, BPM_ERR_CUDA. */
+int bpm_mesh_upload(bpm_ctx* ctx, const double* xyz_nm, int32_t n_nodes,
+                    const int32_t* tets, int32_t n_tets, const int32_t* tet_region,
+                    const bpm_region_mat* mats, int32_t n_regions, uint32_t flags,
+                    int32_t* mesh_id_out);
+int bpm_mesh_info_get(bpm_ctx* ctx, int32_t mesh_id, bpm_mesh_info* out);
+/* Copy one operator (BPM_OP_*) to host memory `dst` in the dense layout
+ * documented at the BPM_OP_* constant. */
+int bpm_mesh_get_operator(bpm_ctx* ctx, int32_t mesh_id, int32_t which, void* dst);
+
+/* Upload a head-field map mu0*H [nz][ny][nx][3] (host, float32).  Voxel
+ * (ix,iy,iz) sits at origin + h*(ix,iy,iz); x is in the head frame, y and z
+ * in the media frame.  Lookups are trilinear, clamped to the grid box.
+ * nx, ny, nz >= 2. */
+int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, int32_t nz,
+                       float h_nm, const float origin_nm[3], int32_t* map_id_out);
+
+/* ---------------------------------------------------------------------- */
+/* Batched LLG (Sec. II.C recording simulations, one batch of islands)     */
+/* ---------------------------------------------------------------------- */
+
+/* Create a batch of B islands that all use the same mesh (isl[b].mesh_id
+ * equal for all b).  Device state is allocated here; the state starts at
+ * m = +z, t = p->t0_ps.  Per step of size h = dt/substeps the batch runs the
+ * Heun predictor and corrector (|m| renormalised after each), each preceded
+ * by one demag GEMM over the whole batch, and updates the switch detector.
+ * Errors: BPM_ERR_ARG (B < 1, mixed meshes, bad map id, substeps < 1). */
+int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B,
+                     const bpm_run_params* p, bpm_batch** out);
+/* Set the state: m (layout above, leading dimension ld) or NULL for +z, the
+ * time t0_ps, and reset the switch detector.  on_device: m is a device
+ * pointer. */
+int bpm_batch_set_state(bpm_batch* bt, const float* m, int32_t ld, double t0_ps, int on_device);
+/* Advance by n_intervals output intervals (stream-ordered; the first call
+ * captures one interval as a CUDA graph, later calls replay it). */
+int bpm_batch_advance(bpm_batch* bt, int32_t n_intervals);
+/* Read the state.  Any output may be NULL.
+ *   m        [B][3][ld] float      switched [B] uint8 (<m_z> <= 0 now)
+ *   t_sw_ps  [B] float, first crossing time, -1 if none
+ *   status   [B] int32 BPM_ISLAND_* bits        mz [B] float, <m_z> now
+ * on_device: all outputs are device pointers (no synchronisation). */
+int bpm_batch_read(bpm_batch* bt, float* m, int32_t ld, uint8_t* switched, float* t_sw_ps,
+                   int32_t* status, float* mz, int on_device);
+/* Effective field B (tesla) of the current state at time t_ps, restricted to
+ * term_mask, into B_out [B][3][ld] (host or device per on_device). */
+int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out, int32_t ld,
+                    int on_device);
+/* Time the kernels of one integrator step with CUDA events on the context
+ * stream: runs `reps` Heun steps launch by launch (outside the graph) and
+ * returns the average duration in ms of one demag GEMM, one predictor stage
+ * and one corrector stage.  The state advances by those steps but the batch
+ * clock does not; call bpm_batch_set_state afterwards to restart a run. */
+int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double* stage1_ms,
+                           double* stage2_ms);
+/* Current simulated time of the batch. */
+int bpm_batch_time(bpm_batch* bt, double* t_ps);
+int bpm_batch_destroy(bpm_batch* bt);
+
+/* One-call form: create, advance from t0 to t0 + n_intervals*dt, read into
+ * host arrays, destroy. */
+int bpm_run_batch(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p,
+                  int32_t n_intervals, float* m_final, int32_t ld, uint8_t* switched,
+                  float* t_sw_ps, int32_t* status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BPM_H */

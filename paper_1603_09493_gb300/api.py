@@ -1,0 +1,214 @@
+"""Thin Python layer over the C ABI: same operations, numpy/torch arguments.
+
+Every computation runs in libbpmllg.so; these classes only own handles and
+convert arguments.  Host arrays are numpy; device arrays are torch CUDA
+tensors (or anything with data_ptr()).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from ctypes import byref, c_double, c_int32, c_void_p
+
+import numpy as np
+
+from . import _lib as L
+
+
+def run_params(p, precision: int = L.PREC_BF16X3, map_id: int = -1) -> L.bpm_run_params:
+    """bpm_run_params from a synth.RunParams-like object."""
+    q = L.bpm_run_params()
+    q.dt_ps = p.dt_ps
+    q.substeps = int(p.substeps)
+    q.precision = int(precision)
+    q.t0_ps = p.t0_ps
+    q.alpha = p.alpha
+    q.rise_ps = p.rise_ps
+    q.v_m_per_s = p.v_m_per_s
+    q.x0_nm = p.x0_nm
+    q.map_id = int(map_id if getattr(p, "use_map", True) else -1)
+    q.term_mask = int(p.term_mask)
+    for c in range(3):
+        q.uniform_T[c] = float(p.uniform_T[c])
+    return q
+
+
+def island_array(isl) -> np.ndarray:
+    """Pack a synth.Islands into the C struct layout (bpm_island[B])."""
+    B = len(isl)
+    a = np.zeros(B, dtype=L.ISLAND_DTYPE)
+    a["mesh_id"] = isl.mesh_id
+    a["Ms_scale"] = isl.Ms_scale
+    a["Ku_scale"] = isl.Ku_scale
+    a["u"] = isl.u
+    a["pos_nm"] = isl.pos_nm
+    a["Hext_T"] = isl.Hext_T
+    return a
+
+
+class Context:
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = L.load()
+        h = c_void_p()
+        s = None if stream is None else c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        L.check(self.lib.bpm_create(byref(h), int(device), s))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.bpm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- meshes
+    def mesh_upload(self, mesh, mats, keep_f64: bool = False) -> int:
+        xyz = np.ascontiguousarray(mesh.xyz_nm, np.float64)
+        tets = np.ascontiguousarray(mesh.tets, np.int32)
+        reg = np.ascontiguousarray(mesh.tet_region, np.int32)
+        mats = np.asarray(mats, np.float64)
+        cm = (L.bpm_region_mat * len(mats))(*[L.bpm_region_mat(*map(float, r)) for r in mats])
+        mid = c_int32()
+        L.check(self.lib.bpm_mesh_upload(self.h, L.ptr(xyz), xyz.shape[0], L.ptr(tets), tets.shape[0],
+                                         L.ptr(reg), ctypes.cast(cm, c_void_p), len(mats),
+                                         L.MESH_KEEP_F64 if keep_f64 else 0, byref(mid)))
+        return mid.value
+
+    def mesh_info(self, mesh_id: int) -> dict:
+        info = L.bpm_mesh_info()
+        L.check(self.lib.bpm_mesh_info_get(self.h, mesh_id, byref(info)))
+        return {f: getattr(info, f) for f, _ in L.bpm_mesh_info._fields_ if f != "pad_"}
+
+    def get_operator(self, mesh_id: int, which: int) -> np.ndarray:
+        n = self.mesh_info(mesh_id)["n_nodes"]
+        shape, dt = {L.OP_EXCHANGE_F32: ((n, n), np.float32), L.OP_DEMAG_F64: ((3 * n, 3 * n), np.float64),
+                     L.OP_DEMAG_F32: ((3 * n, 3 * n), np.float32), L.OP_VOLUMES_F64: ((n,), np.float64),
+                     L.OP_NODAL_MS_F64: ((n,), np.float64), L.OP_NODAL_KU_F64: ((n,), np.float64)}[which]
+        out = np.zeros(shape, dt)
+        L.check(self.lib.bpm_mesh_get_operator(self.h, mesh_id, which, L.ptr(out)))
+        return out
+
+    def headmap_upload(self, hm) -> int:
+        B = np.ascontiguousarray(hm.B_T, np.float32)
+        nz, ny, nx = B.shape[:3]
+        org = np.ascontiguousarray(hm.origin_nm, np.float32)
+        mid = c_int32()
+        L.check(self.lib.bpm_headmap_upload(self.h, L.ptr(B), nx, ny, nz, float(hm.h_nm), L.ptr(org),
+                                            byref(mid)))
+        return mid.value
+
+    # ---- batches
+    def batch(self, islands, params, precision=L.PREC_BF16X3, map_id=-1) -> "Batch":
+        return Batch(self, islands, params, precision, map_id)
+
+    def run_batch(self, islands, params, n_intervals, precision=L.PREC_BF16X3, map_id=-1):
+        isl = island_array(islands)
+        q = run_params(params, precision, map_id)
+        n = self.mesh_info(int(isl["mesh_id"][0]))["n_nodes"]
+        B = len(isl)
+        m = np.zeros((B, 3, n), np.float32)
+        sw = np.zeros(B, np.uint8)
+        tsw = np.zeros(B, np.float32)
+        st = np.zeros(B, np.int32)
+        L.check(self.lib.bpm_run_batch(self.h, L.ptr(isl), B, byref(q), int(n_intervals), L.ptr(m), n,
+                                       L.ptr(sw), L.ptr(tsw), L.ptr(st)))
+        return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st)
+
+
+class Batch:
+    def __init__(self, ctx: Context, islands, params, precision, map_id):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.isl = island_array(islands)
+        self.B = len(self.isl)
+        self.n = ctx.mesh_info(int(self.isl["mesh_id"][0]))["n_nodes"]
+        self.q = run_params(params, precision, map_id)
+        h = c_void_p()
+        L.check(self.lib.bpm_batch_create(ctx.h, L.ptr(self.isl), self.B, byref(self.q), byref(h)))
+        self.h = h
+
+    def destroy(self):
+        if self.h:
+            self.lib.bpm_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+    def set_state(self, m=None, t0_ps: float = 0.0):
+        """m: host numpy [B][3][n] (or a device tensor), None for +z."""
+        on_dev = int(m is not None and hasattr(m, "data_ptr"))
+        ld = self.n if m is None else int(m.shape[-1])
+        if m is not None and not on_dev:
+            m = np.ascontiguousarray(m, np.float32)
+        L.check(self.lib.bpm_batch_set_state(self.h, L.ptr(m), ld, float(t0_ps), on_dev))
+
+    def advance(self, n_intervals: int):
+        L.check(self.lib.bpm_batch_advance(self.h, int(n_intervals)))
+
+    def read(self) -> dict:
+        m = np.zeros((self.B, 3, self.n), np.float32)
+        sw = np.zeros(self.B, np.uint8)
+        tsw = np.zeros(self.B, np.float32)
+        st = np.zeros(self.B, np.int32)
+        mz = np.zeros(self.B, np.float32)
+        L.check(self.lib.bpm_batch_read(self.h, L.ptr(m), self.n, L.ptr(sw), L.ptr(tsw), L.ptr(st), L.ptr(mz), 0))
+        return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st, mz=mz)
+
+    def read_device(self, m, switched, t_sw, status, mz):
+        """Stream-ordered read into device tensors (any may be None)."""
+        ld = self.n if m is None else int(m.shape[-1])
+        L.check(self.lib.bpm_batch_read(self.h, L.ptr(m), ld, L.ptr(switched), L.ptr(t_sw), L.ptr(status),
+                                        L.ptr(mz), 1))
+
+    def field(self, t_ps: float, term_mask: int) -> np.ndarray:
+        out = np.zeros((self.B, 3, self.n), np.float32)
+        L.check(self.lib.bpm_batch_field(self.h, float(t_ps), int(term_mask), L.ptr(out), self.n, 0))
+        return out
+
+    def kernel_times(self, reps: int = 10) -> dict:
+        g, s1, s2 = c_double(), c_double(), c_double()
+        L.check(self.lib.bpm_batch_kernel_times(self.h, int(reps), byref(g), byref(s1), byref(s2)))
+        return dict(gemm_ms=g.value, stage1_ms=s1.value, stage2_ms=s2.value)
+
+    def time(self) -> float:
+        t = c_double()
+        L.check(self.lib.bpm_batch_time(self.h, byref(t)))
+        return t.value
+
+
+def field_bound(ctx: "Context", mesh_id: int, islands, params, head_map=None) -> float:
+    """Upper bound of |B_eff| (T) for a batch: exchange lambda_max (power iteration
+    on the GPU) scaled by the smallest Ms jitter, plus the anisotropy, demag,
+    head, uniform and per-island field bounds."""
+    info = ctx.mesh_info(mesh_id)
+    Ms = ctx.get_operator(mesh_id, L.OP_NODAL_MS_F64)
+    Ku = ctx.get_operator(mesh_id, L.OP_NODAL_KU_F64)
+    Ms_s = np.asarray(islands.Ms_scale, np.float64)
+    Ku_s = np.asarray(islands.Ku_scale, np.float64)
+    b = info["exchange_lambda_max_T"] / Ms_s.min()
+    b += float(np.max(2.0 * Ku / Ms) * np.max(Ku_s / Ms_s))
+    b += 4e-7 * math.pi * float(Ms.max() * Ms_s.max())
+    if head_map is not None and getattr(params, "use_map", True):
+        b += float(np.max(np.linalg.norm(head_map.B_T, axis=-1)))
+    b += float(np.linalg.norm(params.uniform_T)) + float(np.max(np.linalg.norm(islands.Hext_T, axis=1)))
+    return b
+
+
+def stable_substeps(field_bound_T: float, dt_ps: float, alpha: float, courant: float = 0.5) -> int:
+    """Integrator steps per output interval such that gamma/(1+alpha^2) B dt/k <= courant."""
+    gp = 1.76085963023e-1 / (1.0 + alpha * alpha)
+    return max(1, int(math.ceil(gp * field_bound_T * dt_ps / courant)))

@@ -1,0 +1,659 @@
+// C ABI of libbpmllg.so: contexts, mesh and head-map upload, batched LLG runs.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+
+#include "bpm_step.cuh"
+
+namespace bpm {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace bpm
+
+using namespace bpm;
+
+struct bpm_batch {
+    bpm_ctx* ctx = nullptr;
+    Mesh* mesh = nullptr;
+    HeadMap* map = nullptr;
+    int B = 0, Bp = 0;
+    bpm_run_params p{};
+    float4* isl = nullptr;
+    float *m = nullptr, *ms = nullptr, *k1 = nullptr, *Hd = nullptr, *A32 = nullptr;
+    __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr;
+    float *mz_prev = nullptr, *t_sw = nullptr;
+    int *crossed = nullptr, *status = nullptr, *gemm_err = nullptr;
+    long long* interval = nullptr;
+    long long intervals_done = 0;
+    double t0 = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    StepArgs args{};
+};
+
+namespace {
+
+std::vector<bpm_batch*>& live_batches(bpm_ctx* ctx) {
+    static std::vector<std::pair<bpm_ctx*, std::vector<bpm_batch*>>> all;
+    for (auto& e : all)
+        if (e.first == ctx) return e.second;
+    all.push_back({ctx, {}});
+    return all.back().second;
+}
+
+int ensure_device(bpm_ctx* ctx) {
+    BPM_CK(cudaSetDevice(ctx->device));
+    return BPM_OK;
+}
+
+Mesh* get_mesh(bpm_ctx* ctx, int id) {
+    if (!ctx || id < 0 || id >= (int)ctx->meshes.size() || !ctx->meshes[id]) {
+        set_error("unknown mesh id %d", id);
+        return nullptr;
+    }
+    return ctx->meshes[id];
+}
+
+// demag GEMM of the batch's current operand A -> Hd
+int run_demag_gemm(bpm_batch* bt, cudaStream_t s) {
+    Mesh* M = bt->mesh;
+    const int K = M->K();
+    switch (bt->p.precision) {
+        case BPM_PREC_FP32:
+            return gemm_f32_nt(s, bt->Bp, K, K, bt->A32, K, M->N32, K, bt->Hd, K);
+        case BPM_PREC_BF16X3_REF:
+            return gemm_bf16x3_simt(s, bt->Bp, K, K, bt->Ahi, bt->Alo, M->Nhi, M->Nlo, bt->Hd, 3);
+        case BPM_PREC_BF16X3:
+            return gemm_bf16x3_tc(s, bt->Bp, K, K, bt->Ahi, bt->Alo, M->Nhi, M->Nlo, bt->Hd, 3, bt->gemm_err,
+                                  bt->ctx->sm_count);
+        case BPM_PREC_BF16:
+            return gemm_bf16x3_tc(s, bt->Bp, K, K, bt->Ahi, bt->Alo, M->Nhi, M->Nlo, bt->Hd, 1, bt->gemm_err,
+                                  bt->ctx->sm_count);
+        default:
+            set_error("unknown precision %d", bt->p.precision);
+            return BPM_ERR_ARG;
+    }
+}
+
+int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
+    for (int j = 0; j < bt->p.substeps; ++j) {
+        BPM_TRY(run_demag_gemm(bt, s));
+        launch_stage1(bt->args, j, s);
+        BPM_TRY(run_demag_gemm(bt, s));
+        launch_stage2(bt->args, j, s);
+    }
+    launch_interval_tick(bt->interval, s);
+    BPM_CK(cudaGetLastError());
+    return BPM_OK;
+}
+
+void free_batch(bpm_batch* bt) {
+    if (!bt) return;
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    void* ptrs[] = {bt->isl, bt->m, bt->ms, bt->k1, bt->Hd, bt->A32, bt->Ahi, bt->Alo, bt->mz_prev,
+                    bt->t_sw, bt->crossed, bt->status, bt->gemm_err, bt->interval};
+    for (void* p : ptrs) cudaFree(p);
+    delete bt;
+}
+
+template <class T>
+int dalloc(T** p, size_t count) {
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(1, count) * sizeof(T));
+    if (e != cudaSuccess) {
+        set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return BPM_ERR_OOM;
+    }
+    e = cudaMemset(*p, 0, std::max<size_t>(1, count) * sizeof(T));
+    if (e != cudaSuccess) {
+        set_error("cudaMemset failed: %s", cudaGetErrorString(e));
+        return BPM_ERR_CUDA;
+    }
+    return BPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bpm_last_error(void) { return g_err; }
+const char* bpm_version(void) { return "bpmllg 0.1 (sm_103a)"; }
+
+int bpm_create(bpm_ctx** out, int device, void* cuda_stream) {
+    if (!out) {
+        set_error("out is null");
+        return BPM_ERR_ARG;
+    }
+    *out = nullptr;
+    int ndev = 0;
+    BPM_CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) {
+        set_error("device %d not present (%d devices)", device, ndev);
+        return BPM_ERR_ARG;
+    }
+    cudaDeviceProp prop;
+    BPM_CK(cudaGetDeviceProperties(&prop, device));
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        set_error("device %d is sm_%d%d; this library is built for sm_103a only", device, prop.major, prop.minor);
+        return BPM_ERR_CUDA;
+    }
+    BPM_CK(cudaSetDevice(device));
+    BPM_TRY(configure_step_kernels());
+    bpm_ctx* c = new bpm_ctx();
+    c->device = device;
+    c->sm_count = prop.multiProcessorCount;
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
+            return BPM_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return BPM_OK;
+}
+
+void bpm_destroy(bpm_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (bpm_batch* b : live_batches(ctx)) free_batch(b);
+    live_batches(ctx).clear();
+    for (Mesh* m : ctx->meshes) free_mesh(m);
+    for (HeadMap* h : ctx->maps) {
+        if (h) cudaFree(h->B);
+        delete h;
+    }
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int bpm_mesh_upload(bpm_ctx* ctx, const double* xyz_nm, int32_t n_nodes, const int32_t* tets, int32_t n_tets,
+                    const int32_t* tet_region, const bpm_region_mat* mats, int32_t n_regions, uint32_t flags,
+                    int32_t* mesh_id_out) {
+    if (!ctx || !xyz_nm || !tets || !tet_region || !mats || !mesh_id_out) {
+        set_error("null argument");
+        return BPM_ERR_ARG;
+    }
+    if (n_nodes < 4 || n_nodes > kMaxNodes || n_tets < 1 || n_regions < 1) {
+        set_error("mesh sizes out of range: n_nodes=%d (4..%d), n_tets=%d, n_regions=%d", n_nodes, kMaxNodes,
+                  n_tets, n_regions);
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(ctx));
+    Mesh* M = new Mesh();
+    M->n = n_nodes;
+    M->n_pad = round_up(n_nodes, kNodePad);
+    M->n_tets = n_tets;
+    int r = assemble_mesh(ctx, M, xyz_nm, tets, n_tets, tet_region, mats, n_regions, flags);
+    if (r != BPM_OK) {
+        free_mesh(M);
+        return r;
+    }
+    ctx->meshes.push_back(M);
+    *mesh_id_out = (int32_t)ctx->meshes.size() - 1;
+    return BPM_OK;
+}
+
+int bpm_mesh_info_get(bpm_ctx* ctx, int32_t mesh_id, bpm_mesh_info* out) {
+    Mesh* M = get_mesh(ctx, mesh_id);
+    if (!M || !out) return BPM_ERR_ARG;
+    *out = M->info;
+    return BPM_OK;
+}
+
+int bpm_mesh_get_operator(bpm_ctx* ctx, int32_t mesh_id, int32_t which, void* dst) {
+    Mesh* M = get_mesh(ctx, mesh_id);
+    if (!M || !dst) return BPM_ERR_ARG;
+    BPM_TRY(ensure_device(ctx));
+    const int n = M->n, np = M->n_pad;
+    switch (which) {
+        case BPM_OP_EXCHANGE_F32: {
+            float* S = static_cast<float*>(dst);
+            std::memset(S, 0, sizeof(float) * (size_t)n * n);
+            for (int i = 0; i < n; ++i) {
+                double diag = 0;
+                for (int e = M->rowptr[i]; e < M->rowptr[i + 1]; ++e) {
+                    if (M->col[e] == i) continue;
+                    S[(size_t)i * n + M->col[e]] = -M->exch_val[e];
+                    diag += M->exch_val[e];
+                }
+                S[(size_t)i * n + i] = (float)diag;
+            }
+            return BPM_OK;
+        }
+        case BPM_OP_DEMAG_F64:
+            if (!M->N64) {
+                set_error("FP64 demag matrix not kept (upload with BPM_MESH_KEEP_F64)");
+                return BPM_ERR_STATE;
+            }
+            BPM_CK(cudaMemcpy(dst, M->N64, sizeof(double) * 9 * (size_t)n * n, cudaMemcpyDeviceToHost));
+            return BPM_OK;
+        case BPM_OP_DEMAG_F32: {
+            float* D = static_cast<float*>(dst);
+            const int K = M->K();
+            for (int c = 0; c < 3; ++c)
+                for (int c2 = 0; c2 < 3; ++c2)
+                    BPM_CK(cudaMemcpy2D(D + (size_t)c * n * 3 * n + (size_t)c2 * n, 3 * n * sizeof(float),
+                                        M->N32 + (size_t)c * np * K + (size_t)c2 * np, K * sizeof(float),
+                                        n * sizeof(float), n, cudaMemcpyDeviceToHost));
+            return BPM_OK;
+        }
+        case BPM_OP_VOLUMES_F64:
+            std::memcpy(dst, M->V.data(), sizeof(double) * n);
+            return BPM_OK;
+        case BPM_OP_NODAL_MS_F64:
+            std::memcpy(dst, M->Ms.data(), sizeof(double) * n);
+            return BPM_OK;
+        case BPM_OP_NODAL_KU_F64:
+            std::memcpy(dst, M->Ku.data(), sizeof(double) * n);
+            return BPM_OK;
+        default:
+            set_error("unknown operator %d", which);
+            return BPM_ERR_ARG;
+    }
+}
+
+int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, int32_t nz, float h_nm,
+                       const float origin_nm[3], int32_t* map_id_out) {
+    if (!ctx || !B_T || !origin_nm || !map_id_out || nx < 2 || ny < 2 || nz < 2 || !(h_nm > 0)) {
+        set_error("bad head map arguments (need nx, ny, nz >= 2, h > 0)");
+        return BPM_ERR_ARG;
+    }
+    if ((size_t)nx * ny * nz > (size_t)1 << 26) {
+        set_error("head map too large");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(ctx));
+    size_t N = (size_t)nx * ny * nz;
+    std::vector<float4> v(N);
+    for (size_t k = 0; k < N; ++k) v[k] = make_float4(B_T[3 * k], B_T[3 * k + 1], B_T[3 * k + 2], 0.f);
+    HeadMap* H = new HeadMap();
+    H->nx = nx;
+    H->ny = ny;
+    H->nz = nz;
+    H->h = h_nm;
+    for (int a = 0; a < 3; ++a) H->origin[a] = origin_nm[a];
+    cudaError_t e = cudaMalloc(&H->B, N * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemcpy(H->B, v.data(), N * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(H->B);
+        delete H;
+        set_error("head map upload: %s", cudaGetErrorString(e));
+        return BPM_ERR_CUDA;
+    }
+    ctx->maps.push_back(H);
+    *map_id_out = (int32_t)ctx->maps.size() - 1;
+    return BPM_OK;
+}
+
+int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p, bpm_batch** out) {
+    if (!ctx || !isl || !p || !out || B < 1) {
+        set_error("bad batch arguments");
+        return BPM_ERR_ARG;
+    }
+    *out = nullptr;
+    Mesh* M = get_mesh(ctx, isl[0].mesh_id);
+    if (!M) return BPM_ERR_ARG;
+    for (int b = 1; b < B; ++b)
+        if (isl[b].mesh_id != isl[0].mesh_id) {
+            set_error("all islands of a batch must share one mesh (island %d)", b);
+            return BPM_ERR_ARG;
+        }
+    if (p->substeps < 1 || !(p->dt_ps > 0) || p->precision < 0 || p->precision > 3) {
+        set_error("bad run parameters (substeps >= 1, dt > 0, precision 0..3)");
+        return BPM_ERR_ARG;
+    }
+    HeadMap* H = nullptr;
+    if (p->map_id >= 0) {
+        if (p->map_id >= (int)ctx->maps.size()) {
+            set_error("unknown head map id %d", p->map_id);
+            return BPM_ERR_ARG;
+        }
+        H = ctx->maps[p->map_id];
+    }
+    BPM_TRY(ensure_device(ctx));
+    bpm_batch* bt = new bpm_batch();
+    bt->ctx = ctx;
+    bt->mesh = M;
+    bt->map = H;
+    bt->B = B;
+    bt->Bp = round_up(B, kIslandPad);
+    bt->p = *p;
+    bt->t0 = p->t0_ps;
+    const size_t K = (size_t)M->K();
+    const size_t S = (size_t)bt->Bp * K;
+    int r = BPM_OK;
+    auto chk = [&](int rr) {
+        if (r == BPM_OK) r = rr;
+    };
+    chk(dalloc(&bt->isl, 3 * (size_t)B));
+    chk(dalloc(&bt->m, S));
+    chk(dalloc(&bt->ms, S));
+    chk(dalloc(&bt->k1, S));
+    chk(dalloc(&bt->Hd, S));
+    if (p->precision == BPM_PREC_FP32)
+        chk(dalloc(&bt->A32, S));
+    else {
+        chk(dalloc(&bt->Ahi, S));
+        chk(dalloc(&bt->Alo, S));
+    }
+    chk(dalloc(&bt->mz_prev, B));
+    chk(dalloc(&bt->t_sw, B));
+    chk(dalloc(&bt->crossed, B));
+    chk(dalloc(&bt->status, B));
+    chk(dalloc(&bt->gemm_err, 4));
+    chk(dalloc(&bt->interval, 1));
+    if (r != BPM_OK) {
+        free_batch(bt);
+        return r;
+    }
+    std::vector<float4> ip(3 * (size_t)B);
+    for (int b = 0; b < B; ++b) {
+        const bpm_island& I = isl[b];
+        if (!(I.Ms_scale > 0) || !(I.Ku_scale >= 0)) {
+            free_batch(bt);
+            set_error("island %d: Ms_scale must be > 0 and Ku_scale >= 0", b);
+            return BPM_ERR_ARG;
+        }
+        ip[3 * b] = make_float4(1.f / I.Ms_scale, I.Ku_scale / I.Ms_scale, I.Ms_scale, 0.f);
+        ip[3 * b + 1] = make_float4(I.u[0], I.u[1], I.u[2], I.pos_nm[0]);
+        ip[3 * b + 2] = make_float4(I.pos_nm[1], I.Hext_T[0], I.Hext_T[1], I.Hext_T[2]);
+    }
+    cudaError_t e = cudaMemcpy(bt->isl, ip.data(), ip.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_batch(bt);
+        set_error("island upload: %s", cudaGetErrorString(e));
+        return BPM_ERR_CUDA;
+    }
+    StepArgs& a = bt->args;
+    a.B = B;
+    a.n = M->n;
+    a.n_pad = M->n_pad;
+    a.node_pos = M->node_pos;
+    a.node_mat = M->node_mat;
+    a.sell_off = M->sell_off;
+    a.sell_ent = M->sell_ent;
+    a.isl = bt->isl;
+    a.map = H ? H->B : nullptr;
+    a.mx = H ? H->nx : 2;
+    a.my = H ? H->ny : 2;
+    a.mz = H ? H->nz : 2;
+    a.mh = H ? H->h : 1.f;
+    a.mox = H ? H->origin[0] : 0.f;
+    a.moy = H ? H->origin[1] : 0.f;
+    a.moz = H ? H->origin[2] : 0.f;
+    a.m = bt->m;
+    a.ms = bt->ms;
+    a.k1 = bt->k1;
+    a.Hd = bt->Hd;
+    a.A32 = bt->A32;
+    a.Ahi = bt->Ahi;
+    a.Alo = bt->Alo;
+    a.prec = p->precision;
+    a.mz_prev = bt->mz_prev;
+    a.t_sw = bt->t_sw;
+    a.crossed = bt->crossed;
+    a.status = bt->status;
+    a.interval = bt->interval;
+    a.t0 = p->t0_ps;
+    a.k = p->substeps;
+    a.h = p->dt_ps / p->substeps;
+    a.alpha = (float)p->alpha;
+    a.gp = (float)(kGammaPs / (1.0 + p->alpha * p->alpha));
+    a.rise = (float)p->rise_ps;
+    a.v_nm_ps = (float)(p->v_m_per_s * 1e-3);
+    a.x0 = (float)p->x0_nm;
+    for (int c = 0; c < 3; ++c) a.uni[c] = p->uniform_T[c];
+    a.mask = p->term_mask;
+    live_batches(ctx).push_back(bt);
+    r = bpm_batch_set_state(bt, nullptr, 0, p->t0_ps, 0);
+    if (r != BPM_OK) {
+        bpm_batch_destroy(bt);
+        return r;
+    }
+    *out = bt;
+    return BPM_OK;
+}
+
+namespace {
+__global__ void k_fill_plus_z(int B, int n, int n_pad, float* m) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = blockIdx.y;
+    if (i >= n) return;
+    size_t base = (size_t)b * 3 * n_pad;
+    m[base + i] = 0.f;
+    m[base + n_pad + i] = 0.f;
+    m[base + 2 * n_pad + i] = 1.f;
+}
+__global__ void k_read_flags(int B, const float* mz_prev, const float* t_sw, const int* status,
+                             uint8_t* switched, float* tsw_out, int* status_out, float* mz_out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    if (switched) switched[b] = mz_prev[b] <= 0.f ? 1 : 0;
+    if (tsw_out) tsw_out[b] = t_sw[b];
+    if (status_out) status_out[b] = status[b];
+    if (mz_out) mz_out[b] = mz_prev[b];
+}
+}  // namespace
+
+int bpm_batch_set_state(bpm_batch* bt, const float* m, int32_t ld, double t0_ps, int on_device) {
+    if (!bt) {
+        set_error("null batch");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    cudaStream_t s = bt->ctx->stream;
+    const int n = bt->mesh->n, np = bt->mesh->n_pad;
+    if (m) {
+        if (ld < n) {
+            set_error("ld %d < n_nodes %d", ld, n);
+            return BPM_ERR_ARG;
+        }
+        BPM_CK(cudaMemcpy2DAsync(bt->m, np * sizeof(float), m, ld * sizeof(float), n * sizeof(float),
+                                 3 * (size_t)bt->B, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 s));
+    } else {
+        k_fill_plus_z<<<dim3((n + 255) / 256, bt->B), 256, 0, s>>>(bt->B, n, np, bt->m);
+    }
+    BPM_CK(cudaMemsetAsync(bt->interval, 0, sizeof(long long), s));
+    bt->t0 = t0_ps;
+    bt->args.t0 = t0_ps;
+    bt->intervals_done = 0;
+    // the interval graph bakes t0 into its kernel arguments: drop it
+    if (bt->exec) {
+        cudaGraphExecDestroy(bt->exec);
+        bt->exec = nullptr;
+    }
+    if (bt->graph) {
+        cudaGraphDestroy(bt->graph);
+        bt->graph = nullptr;
+    }
+    launch_init(bt->args, s);
+    BPM_CK(cudaGetLastError());
+    if (!on_device) BPM_CK(cudaStreamSynchronize(s));
+    return BPM_OK;
+}
+
+int bpm_batch_advance(bpm_batch* bt, int32_t n_intervals) {
+    if (!bt || n_intervals < 0) {
+        set_error("bad advance arguments");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    cudaStream_t s = bt->ctx->stream;
+    if (!bt->exec && n_intervals > 0) {
+        BPM_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int r = enqueue_interval(bt, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (r != BPM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) {
+            set_error("graph capture failed: %s", cudaGetErrorString(e));
+            return BPM_ERR_CUDA;
+        }
+        bt->graph = g;
+        BPM_CK(cudaGraphInstantiate(&bt->exec, g, 0));
+    }
+    for (int i = 0; i < n_intervals; ++i) BPM_CK(cudaGraphLaunch(bt->exec, s));
+    bt->intervals_done += n_intervals;
+    return BPM_OK;
+}
+
+int bpm_batch_read(bpm_batch* bt, float* m, int32_t ld, uint8_t* switched, float* t_sw_ps, int32_t* status,
+                   float* mz, int on_device) {
+    if (!bt) {
+        set_error("null batch");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    cudaStream_t s = bt->ctx->stream;
+    const int n = bt->mesh->n, np = bt->mesh->n_pad, B = bt->B;
+    if (m) {
+        if (ld < n) {
+            set_error("ld %d < n_nodes %d", ld, n);
+            return BPM_ERR_ARG;
+        }
+        BPM_CK(cudaMemcpy2DAsync(m, ld * sizeof(float), bt->m, np * sizeof(float), n * sizeof(float), 3 * (size_t)B,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    }
+    if (on_device) {
+        k_read_flags<<<(B + 255) / 256, 256, 0, s>>>(B, bt->mz_prev, bt->t_sw, bt->status, switched, t_sw_ps,
+                                                    status, mz);
+        BPM_CK(cudaGetLastError());
+        return BPM_OK;
+    }
+    std::vector<float> mzv(B), tsw(B);
+    std::vector<int> st(B);
+    BPM_CK(cudaMemcpyAsync(mzv.data(), bt->mz_prev, B * sizeof(float), cudaMemcpyDeviceToHost, s));
+    BPM_CK(cudaMemcpyAsync(tsw.data(), bt->t_sw, B * sizeof(float), cudaMemcpyDeviceToHost, s));
+    BPM_CK(cudaMemcpyAsync(st.data(), bt->status, B * sizeof(int), cudaMemcpyDeviceToHost, s));
+    BPM_CK(cudaStreamSynchronize(s));
+    for (int b = 0; b < B; ++b) {
+        if (switched) switched[b] = mzv[b] <= 0.f ? 1 : 0;
+        if (t_sw_ps) t_sw_ps[b] = tsw[b];
+        if (status) status[b] = st[b];
+        if (mz) mz[b] = mzv[b];
+    }
+    return BPM_OK;
+}
+
+int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out, int32_t ld, int on_device) {
+    if (!bt || !B_out || ld < (bt ? bt->mesh->n : 0)) {
+        set_error("bad field arguments");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    cudaStream_t s = bt->ctx->stream;
+    const int n = bt->mesh->n, np = bt->mesh->n_pad;
+    float* out = nullptr;
+    BPM_CK(cudaMallocAsync(&out, (size_t)bt->Bp * 3 * np * sizeof(float), s));
+    int r = BPM_OK;
+    if (term_mask & BPM_TERM_DEMAG) r = run_demag_gemm(bt, s);
+    if (r == BPM_OK) {
+        launch_field(bt->args, t_ps, term_mask, out, s);
+        cudaError_t e = cudaMemcpy2DAsync(B_out, ld * sizeof(float), out, np * sizeof(float), n * sizeof(float),
+                                          3 * (size_t)bt->B,
+                                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
+            set_error("field copy: %s", cudaGetErrorString(e));
+            r = BPM_ERR_CUDA;
+        }
+    }
+    cudaFreeAsync(out, s);
+    if (r != BPM_OK) return r;
+    if (!on_device) BPM_CK(cudaStreamSynchronize(s));
+    return BPM_OK;
+}
+
+int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double* stage1_ms,
+                           double* stage2_ms) {
+    if (!bt || reps < 1) {
+        set_error("bad kernel timing arguments");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    cudaStream_t s = bt->ctx->stream;
+    cudaEvent_t ev[5];
+    for (auto& e : ev) BPM_CK(cudaEventCreate(&e));
+    double acc[3] = {0, 0, 0};
+    int r = BPM_OK;
+    for (int q = 0; q < reps && r == BPM_OK; ++q) {
+        int j = q % bt->p.substeps;
+        cudaEventRecord(ev[0], s);
+        r = run_demag_gemm(bt, s);
+        cudaEventRecord(ev[1], s);
+        launch_stage1(bt->args, j, s);
+        cudaEventRecord(ev[2], s);
+        if (r == BPM_OK) r = run_demag_gemm(bt, s);
+        cudaEventRecord(ev[3], s);
+        launch_stage2(bt->args, j, s);
+        cudaEventRecord(ev[4], s);
+        cudaError_t e = cudaEventSynchronize(ev[4]);
+        if (e != cudaSuccess) {
+            set_error("kernel timing: %s", cudaGetErrorString(e));
+            r = BPM_ERR_CUDA;
+            break;
+        }
+        float t[4];
+        for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
+        acc[0] += 0.5 * (t[0] + t[2]);
+        acc[1] += t[1];
+        acc[2] += t[3];
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (r != BPM_OK) return r;
+    if (gemm_ms) *gemm_ms = acc[0] / reps;
+    if (stage1_ms) *stage1_ms = acc[1] / reps;
+    if (stage2_ms) *stage2_ms = acc[2] / reps;
+    return BPM_OK;
+}
+
+int bpm_batch_time(bpm_batch* bt, double* t_ps) {
+    if (!bt || !t_ps) {
+        set_error("null argument");
+        return BPM_ERR_ARG;
+    }
+    *t_ps = bt->t0 + bt->intervals_done * bt->p.dt_ps;
+    return BPM_OK;
+}
+
+int bpm_batch_destroy(bpm_batch* bt) {
+    if (!bt) return BPM_OK;
+    cudaSetDevice(bt->ctx->device);
+    cudaStreamSynchronize(bt->ctx->stream);
+    auto& v = live_batches(bt->ctx);
+    v.erase(std::remove(v.begin(), v.end(), bt), v.end());
+    free_batch(bt);
+    return BPM_OK;
+}
+
+int bpm_run_batch(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p, int32_t n_intervals,
+                  float* m_final, int32_t ld, uint8_t* switched, float* t_sw_ps, int32_t* status) {
+    bpm_batch* bt = nullptr;
+    BPM_TRY(bpm_batch_create(ctx, isl, B, p, &bt));
+    int r = bpm_batch_advance(bt, n_intervals);
+    if (r == BPM_OK) r = bpm_batch_read(bt, m_final, ld, switched, t_sw_ps, status, nullptr, 0);
+    bpm_batch_destroy(bt);
+    return r;
+}
+
+}  // extern "C"

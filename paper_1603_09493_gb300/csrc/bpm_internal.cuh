@@ -1,0 +1,100 @@
+// Internal declarations shared by the translation units of libbpmllg.so.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/bpm.h"
+
+namespace bpm {
+
+constexpr double kMu0 = 1.25663706143591729e-6;       // 4 pi 1e-7 T m / A
+constexpr double kGammaPs = 1.76085963023e-1;         // rad / (ps T)
+constexpr int kMaxNodes = 8192;
+constexpr int kNodePad = 64;                           // n_pad multiple (3 n_pad is a multiple of 64)
+constexpr int kIslandPad = 128;                        // batch rows padded to the GEMM M tile
+
+void set_error(const char* fmt, ...);
+
+#define BPM_CK(call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            bpm::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                  \
+                           cudaGetErrorString(e_));                                    \
+            return (e_ == cudaErrorMemoryAllocation) ? BPM_ERR_OOM : BPM_ERR_CUDA;     \
+        }                                                                              \
+    } while (0)
+
+#define BPM_TRY(expr)              \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ != BPM_OK) return r_; \
+    } while (0)
+
+// Device-resident operators of one island mesh.
+struct Mesh {
+    int n = 0, n_pad = 0, n_tets = 0, nb = 0, nnz = 0;
+    // per node (padded to n_pad; padding nodes have w = 0 and no neighbours)
+    float4* node_pos = nullptr;   // x, y, z (nm), w_i = V_i / sum V
+    float4* node_mat = nullptr;   // 2 Ku_i / Ms_i (T), Ms_i (MA/m), 0, 0
+    // exchange operator, difference form, sliced ELL with 32-row slices:
+    // B_ex,i = (1/Ms_scale) sum_e val_e (m_{col_e} - m_i); padding entries val = 0, col = i
+    int n_slices = 0;
+    int* sell_off = nullptr;      // [n_slices + 1] first entry of each slice
+    int2* sell_ent = nullptr;     // (col, float bits of val), entry e of row 32 s + l at off[s] + 32 e + l
+    // demag operator -mu0*1e6*N, row c*n_pad+i, column c'*n_pad+k (T per MA/m)
+    float* N32 = nullptr;         // [K][K]
+    __nv_bfloat16* Nhi = nullptr; // [K][K]
+    __nv_bfloat16* Nlo = nullptr; // [K][K]
+    double* N64 = nullptr;        // [3n][3n] compact, H = -N M (only with BPM_MESH_KEEP_F64)
+    // host copies for export
+    std::vector<int> rowptr, col; // CSR pattern incl. diagonal
+    std::vector<float> exch_val;  // c_ij per CSR entry (0 on the diagonal)
+    std::vector<double> V, Ms, Ku;
+    bpm_mesh_info info{};
+    int K() const { return 3 * n_pad; }
+};
+
+struct HeadMap {
+    float4* B = nullptr;          // [nz][ny][nx] (Bx, By, Bz, 0)
+    int nx = 0, ny = 0, nz = 0;
+    float h = 1.f;
+    float origin[3] = {0, 0, 0};
+};
+
+}  // namespace bpm
+
+struct bpm_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<bpm::Mesh*> meshes;
+    std::vector<bpm::HeadMap*> maps;
+};
+
+namespace bpm {
+
+// assembly (bpm_assemble.cu)
+int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets, int32_t n_tets,
+                  const int32_t* region, const bpm_region_mat* mats, int32_t n_regions,
+                  uint32_t flags);
+void free_mesh(Mesh* M);
+
+// demag GEMMs: C[M_rows][Nout] = A[M_rows][K] * W[Nout][K]^T, row strides lda/ldw/ldc (elements)
+int gemm_f32_nt(cudaStream_t s, int M_rows, int Nout, int K, const float* A, int lda,
+                const float* W, int ldw, float* C, int ldc);
+int gemm_bf16x3_simt(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi,
+                     const __nv_bfloat16* Alo, const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo,
+                     float* C, int products);
+int gemm_bf16x3_tc(cudaStream_t s, int M_rows, int Nout, int K, const __nv_bfloat16* Ahi,
+                   const __nv_bfloat16* Alo, const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo,
+                   float* C, int products, int* err_flag, int sm_count);
+
+}  // namespace bpm

@@ -1,0 +1,275 @@
+// Heun stage kernels of the batched LLG step, one CTA per island.
+//
+// LLG at 0 K (Sec. II.A; Landau-Lifshitz form with Gilbert damping):
+//   dm/dt = -gamma/(1+alpha^2) [m x B + alpha m x (m x B)]
+// with B = B_ex + B_an + B_d + ramp(t) (B_head + B_uniform) + B_ext, the head
+// map moved at the head velocity and scaled by the field rise (Sec. II.A,
+// II.C).  Heun: k1 = f(m_n, t_n), m* = N(m_n + h k1), k2 = f(m*, t_n + h),
+// m_{n+1} = N(m_n + h/2 (k1 + k2)), N(v) = v/|v|.
+//
+// Stage 1 (predictor) and stage 2 (corrector) each stage the island's source
+// state in shared memory for the exchange gather, evaluate the local field
+// terms, take the Heun stage, renormalise, and write the demag GEMM operand of
+// the new state (Ms * m, FP32 or BF16 hi/lo).  Stage 2 also updates the
+// volume-averaged <m_z> switch detector with a fixed-order block reduction.
+// The demag field B_d of the stage's source state comes from the GEMM that
+// ran just before the stage.
+#include "bpm_step.cuh"
+
+namespace bpm {
+
+namespace {
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize3(float3 v) {
+    float r = rsqrtf(dot3(v, v));
+    return r * v;
+}
+
+__device__ __forceinline__ float3 trilinear(const StepArgs& a, float px, float py, float pz) {
+    float fx = (px - a.mox) / a.mh, fy = (py - a.moy) / a.mh, fz = (pz - a.moz) / a.mh;
+    fx = fminf(fmaxf(fx, 0.f), (float)(a.mx - 1));
+    fy = fminf(fmaxf(fy, 0.f), (float)(a.my - 1));
+    fz = fminf(fmaxf(fz, 0.f), (float)(a.mz - 1));
+    int ix = min((int)floorf(fx), a.mx - 2), iy = min((int)floorf(fy), a.my - 2),
+        iz = min((int)floorf(fz), a.mz - 2);
+    float wx = fx - ix, wy = fy - iy, wz = fz - iz;
+    float3 acc = f3(0, 0, 0);
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                float w = (dx ? wx : 1.f - wx) * (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
+                float4 v = __ldg(a.map + ((size_t)(iz + dz) * a.my + (iy + dy)) * a.mx + (ix + dx));
+                acc = acc + w * f3(v.x, v.y, v.z);
+            }
+    return acc;
+}
+
+// effective field at node i of island b from the source state staged in smem
+__device__ __forceinline__ float3 eff_field(const StepArgs& a, int b, int i, float3 mi, const float* sm,
+                                            float4 p0, float4 p1, float4 p2, float ramp, float xh,
+                                            unsigned mask) {
+    float3 B = f3(0, 0, 0);
+    const int np = a.n_pad;
+    if (mask & BPM_TERM_EXCHANGE) {
+        int s = i >> 5, l = i & 31;
+        int off = __ldg(a.sell_off + s);
+        int w = (__ldg(a.sell_off + s + 1) - off) >> 5;
+        const int2* ep = a.sell_ent + off + l;
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        for (int e = 0; e < w; ++e) {
+            int2 c = __ldg(ep + 32 * e);
+            float v = __int_as_float(c.y);
+            bx += v * (sm[c.x] - mi.x);
+            by += v * (sm[np + c.x] - mi.y);
+            bz += v * (sm[2 * np + c.x] - mi.z);
+        }
+        B = B + p0.x * f3(bx, by, bz);
+    }
+    if (mask & BPM_TERM_ANISOTROPY) {
+        float3 u = f3(p1.x, p1.y, p1.z);
+        float an = __ldg(&a.node_mat[i].x) * p0.y;
+        B = B + (an * dot3(mi, u)) * u;
+    }
+    if (mask & BPM_TERM_DEMAG) {
+        const float* hd = a.Hd + (size_t)b * 3 * np + i;
+        B = B + f3(hd[0], hd[np], hd[2 * np]);
+    }
+    if ((mask & BPM_TERM_HEAD) && a.map) {
+        float4 pos = __ldg(a.node_pos + i);
+        B = B + ramp * trilinear(a, pos.x + p1.w - xh, pos.y + p2.x, pos.z);
+    }
+    if (mask & BPM_TERM_UNIFORM) {
+        B = B + ramp * f3(a.uni[0], a.uni[1], a.uni[2]) + f3(p2.y, p2.z, p2.w);
+    }
+    return B;
+}
+
+__device__ __forceinline__ float3 llg_rhs(float3 m, float3 B, float alpha, float gp) {
+    float3 mxB = cross3(m, B);
+    float3 t = mxB + alpha * cross3(m, mxB);
+    return (-gp) * t;
+}
+
+__device__ __forceinline__ void write_gemm_input(const StepArgs& a, int b, int i, float3 v, float msi) {
+    const size_t K = 3 * (size_t)a.n_pad;
+    size_t o = (size_t)b * K + i;
+    float x[3] = {msi * v.x, msi * v.y, msi * v.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        size_t oc = o + (size_t)c * a.n_pad;
+        if (a.prec == BPM_PREC_FP32) {
+            a.A32[oc] = x[c];
+        } else {
+            __nv_bfloat16 hi = __float2bfloat16_rn(x[c]);
+            a.Ahi[oc] = hi;
+            a.Alo[oc] = __float2bfloat16_rn(x[c] - __bfloat162float(hi));
+        }
+    }
+}
+
+__device__ __forceinline__ void stage_to_smem(const float* src, float* sm, int n_pad) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(sm);
+    for (int q = threadIdx.x; q < 3 * n_pad / 4; q += blockDim.x) d4[q] = s4[q];
+}
+
+__device__ __forceinline__ float block_reduce(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+__device__ __forceinline__ double step_time(const StepArgs& a, int j) {
+    long long it = *a.interval;
+    return a.t0 + (double)(it * a.k + j) * a.h;
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_stage1(StepArgs a, int j) {
+    extern __shared__ float sm[];
+    const int b = blockIdx.x;
+    const int np = a.n_pad;
+    const size_t base = (size_t)b * 3 * np;
+    stage_to_smem(a.m + base, sm, np);
+    const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
+    const double t = step_time(a, j);
+    const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
+    const float xh = a.x0 + a.v_nm_ps * (float)t;
+    const float hf = (float)a.h;
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
+        float3 B = eff_field(a, b, i, mi, sm, p0, p1, p2, ramp, xh, a.mask);
+        float3 f = llg_rhs(mi, B, a.alpha, a.gp);
+        float3 v = normalize3(mi + hf * f);
+        a.k1[base + i] = f.x;
+        a.k1[base + np + i] = f.y;
+        a.k1[base + 2 * np + i] = f.z;
+        a.ms[base + i] = v.x;
+        a.ms[base + np + i] = v.y;
+        a.ms[base + 2 * np + i] = v.z;
+        write_gemm_input(a, b, i, v, __ldg(&a.node_mat[i].y) * p0.z);
+    }
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_stage2(StepArgs a, int j) {
+    extern __shared__ float sm[];
+    __shared__ float red[kStepThreads / 32];
+    const int b = blockIdx.x;
+    const int np = a.n_pad;
+    const size_t base = (size_t)b * 3 * np;
+    stage_to_smem(a.ms + base, sm, np);
+    const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
+    const double t = step_time(a, j) + a.h;
+    const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
+    const float xh = a.x0 + a.v_nm_ps * (float)t;
+    const float hh = 0.5f * (float)a.h;
+    __syncthreads();
+    float mzp = 0.f;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
+        float3 B = eff_field(a, b, i, mi, sm, p0, p1, p2, ramp, xh, a.mask);
+        float3 f2 = llg_rhs(mi, B, a.alpha, a.gp);
+        float3 mn = f3(a.m[base + i], a.m[base + np + i], a.m[base + 2 * np + i]);
+        float3 f1 = f3(a.k1[base + i], a.k1[base + np + i], a.k1[base + 2 * np + i]);
+        float3 v = normalize3(mn + hh * (f1 + f2));
+        a.m[base + i] = v.x;
+        a.m[base + np + i] = v.y;
+        a.m[base + 2 * np + i] = v.z;
+        write_gemm_input(a, b, i, v, __ldg(&a.node_mat[i].y) * p0.z);
+        mzp += __ldg(&a.node_pos[i].w) * v.z;
+    }
+    float mz = block_reduce(mzp, red);
+    if (threadIdx.x == 0) {
+        float prev = a.mz_prev[b];
+        if (!a.crossed[b] && mz <= 0.f) {
+            double d = (double)prev - (double)mz;
+            double frac = d > 0 ? (double)prev / d : 1.0;
+            a.t_sw[b] = (float)(t - a.h + a.h * frac);
+            a.crossed[b] = 1;
+        }
+        a.mz_prev[b] = mz;
+        if (!isfinite(mz)) a.status[b] |= BPM_ISLAND_NONFINITE;
+    }
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_init(StepArgs a) {
+    __shared__ float red[kStepThreads / 32];
+    const int b = blockIdx.x;
+    const int np = a.n_pad;
+    const size_t base = (size_t)b * 3 * np;
+    const float4 p0 = a.isl[3 * b];
+    float mzp = 0.f;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        float3 v = f3(a.m[base + i], a.m[base + np + i], a.m[base + 2 * np + i]);
+        write_gemm_input(a, b, i, v, __ldg(&a.node_mat[i].y) * p0.z);
+        mzp += __ldg(&a.node_pos[i].w) * v.z;
+    }
+    float mz = block_reduce(mzp, red);
+    if (threadIdx.x == 0) {
+        a.mz_prev[b] = mz;
+        a.crossed[b] = mz <= 0.f ? 1 : 0;
+        a.t_sw[b] = mz <= 0.f ? (float)a.t0 : -1.f;
+        a.status[b] = isfinite(mz) ? 0 : BPM_ISLAND_NONFINITE;
+    }
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_field(StepArgs a, double t, unsigned mask, float* out) {
+    extern __shared__ float sm[];
+    const int b = blockIdx.x;
+    const int np = a.n_pad;
+    const size_t base = (size_t)b * 3 * np;
+    stage_to_smem(a.m + base, sm, np);
+    const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
+    const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
+    const float xh = a.x0 + a.v_nm_ps * (float)t;
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
+        float3 B = eff_field(a, b, i, mi, sm, p0, p1, p2, ramp, xh, mask);
+        out[base + i] = B.x;
+        out[base + np + i] = B.y;
+        out[base + 2 * np + i] = B.z;
+    }
+}
+
+__global__ void k_tick(long long* interval) { *interval += 1; }
+
+}  // namespace
+
+int configure_step_kernels() {
+    int smem = 3 * kMaxNodes * (int)sizeof(float);
+    BPM_CK(cudaFuncSetAttribute(k_stage1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return BPM_OK;
+}
+
+static size_t smem_bytes(const StepArgs& a) { return 3 * (size_t)a.n_pad * sizeof(float); }
+
+void launch_stage1(const StepArgs& a, int j, cudaStream_t s) {
+    k_stage1<<<a.B, kStepThreads, smem_bytes(a), s>>>(a, j);
+}
+void launch_stage2(const StepArgs& a, int j, cudaStream_t s) {
+    k_stage2<<<a.B, kStepThreads, smem_bytes(a), s>>>(a, j);
+}
+void launch_init(const StepArgs& a, cudaStream_t s) { k_init<<<a.B, kStepThreads, 0, s>>>(a); }
+void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaStream_t s) {
+    k_field<<<a.B, kStepThreads, smem_bytes(a), s>>>(a, t, mask, out);
+}
+void launch_interval_tick(long long* interval, cudaStream_t s) { k_tick<<<1, 1, 0, s>>>(interval); }
+
+}  // namespace bpm

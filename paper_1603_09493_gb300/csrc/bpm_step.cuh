@@ -1,0 +1,47 @@
+// Per-island Heun stage kernels: declarations shared by the API layer.
+#pragma once
+#include "bpm_internal.cuh"
+
+namespace bpm {
+
+struct StepArgs {
+    int B, n, n_pad;
+    const float4* node_pos;   // [n_pad] x, y, z, w
+    const float4* node_mat;   // [n_pad] 2Ku/Ms (T), Ms (MA/m)
+    const int* sell_off;
+    const int2* sell_ent;
+    const float4* isl;        // [B][3] (1/Ms_s, Ku_s/Ms_s, Ms_s, 0), (u, pos_x), (pos_y, Hext)
+    const float4* map;        // head map or nullptr
+    int mx, my, mz;
+    float mh, mox, moy, moz;
+    float* m;                 // [Bp][3][n_pad]
+    float* ms;                // predictor state m*
+    float* k1;                // predictor slope
+    const float* Hd;          // demag field of the GEMM input state, tesla
+    float* A32;               // GEMM input (FP32), [Bp][3 n_pad], Ms * m in MA/m
+    __nv_bfloat16* Ahi;       // GEMM input BF16 hi/lo split
+    __nv_bfloat16* Alo;
+    int prec;
+    float* mz_prev;           // [B] detector state
+    float* t_sw;
+    int* crossed;
+    int* status;
+    const long long* interval;  // device interval counter
+    double t0, h;
+    int k;                    // steps per interval
+    float alpha, gp;          // damping, gamma/(1+alpha^2) in rad/(ps T)
+    float rise, v_nm_ps, x0;
+    float uni[3];
+    unsigned mask;
+};
+
+constexpr int kStepThreads = 256;
+
+void launch_stage1(const StepArgs& a, int j, cudaStream_t s);
+void launch_stage2(const StepArgs& a, int j, cudaStream_t s);
+void launch_init(const StepArgs& a, cudaStream_t s);
+void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaStream_t s);
+void launch_interval_tick(long long* interval, cudaStream_t s);
+int configure_step_kernels();
+
+}  // namespace bpm

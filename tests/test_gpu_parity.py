@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (from the arithmetic, stated per check):
+* assembly is FP64 on the GPU vs FP64 dense LU in the oracle: the batched CG
+  stops at a 1e-12 relative residual, so N agrees to ~1e-9 of max|N|;
+* FP32 field terms: single rounding of each stored operand and FP32
+  accumulation, ~1e-6 relative to the term's scale;
+* BF16 hi/lo split demag: operands carry ~16 mantissa bits, ~1e-5 relative;
+* dynamics: max |dm| <= 1e-3 over the first 100 ps, identical switch outcome,
+  |dt_sw| <= 2 ps (the acceptance bar of the batched mixed-precision path).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fem, llg
+from paper_1603_09493_gb300 import _lib as L
+from paper_1603_09493_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+MU0 = 4e-7 * math.pi
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not os.path.exists(L.LIB_PATH):
+        from paper_1603_09493_gb300 import build
+        build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def small(ctx):
+    mesh = synth.small_island_mesh()
+    mats = synth.ecc_materials()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    mid = ctx.mesh_upload(mesh, mats, keep_f64=True)
+    return mesh, mats, ops, mid
+
+
+@pytest.fixture(scope="module")
+def headmap(ctx):
+    hm = synth.synthetic_head_map()
+    return hm, ctx.headmap_upload(hm)
+
+
+def _check_assembly(ctx, ops, mid):
+    info = ctx.mesh_info(mid)
+    assert info["n_nodes"] == ops.n
+    V = ctx.get_operator(mid, L.OP_VOLUMES_F64)
+    Ms = ctx.get_operator(mid, L.OP_NODAL_MS_F64)
+    Ku = ctx.get_operator(mid, L.OP_NODAL_KU_F64)
+    assert np.allclose(V, ops.V, rtol=1e-12, atol=0)
+    assert np.allclose(Ms, ops.Ms, rtol=1e-12, atol=0)
+    assert np.allclose(Ku, ops.Ku, rtol=1e-12, atol=1e-6)
+    S = ctx.get_operator(mid, L.OP_EXCHANGE_F32).astype(np.float64)
+    assert np.abs(S - ops.S).max() <= 2e-6 * np.abs(ops.S).max()
+    N64 = ctx.get_operator(mid, L.OP_DEMAG_F64)
+    assert np.abs(N64 - ops.demag).max() <= 1e-9 * np.abs(ops.demag).max()
+    N32 = ctx.get_operator(mid, L.OP_DEMAG_F32).astype(np.float64)
+    ref = -MU0 * 1e6 * ops.demag
+    assert np.abs(N32 - ref).max() <= 1e-6 * np.abs(ref).max()
+    lam = ops.exchange_lambda_max()
+    assert abs(info["exchange_lambda_max_T"] - lam) <= 1e-3 * lam
+    assert info["cg_residual_neumann"] < 1e-12 and info["cg_residual_dirichlet"] < 1e-12
+    assert abs(info["volume_nm3"] - ops.V.sum()) < 1e-9 * ops.V.sum()
+
+
+def test_assembly_small_mesh(ctx, small):
+    _, _, ops, mid = small
+    _check_assembly(ctx, ops, mid)
+
+
+def test_assembly_census_mesh(ctx):
+    mesh = synth.census_island_mesh()
+    mats = synth.ecc_materials()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    mid = ctx.mesh_upload(mesh, mats, keep_f64=True)
+    _check_assembly(ctx, ops, mid)
+
+
+def _smooth_state(xyz, B, seed):
+    rng = np.random.default_rng(seed)
+    m = np.zeros((B, xyz.shape[0], 3))
+    for b in range(B):
+        a = rng.uniform(-0.6, 0.6, size=(3, 3))
+        m[b] = np.stack([a[0, 0] * np.sin(0.4 * xyz[:, 0] + a[0, 1]) + a[0, 2] * 0.1 * xyz[:, 2],
+                         a[1, 0] * np.cos(0.3 * xyz[:, 1] + a[1, 1]),
+                         np.ones(xyz.shape[0]) + a[2, 0] * 0.05 * xyz[:, 2]], 1)
+    return m / np.linalg.norm(m, axis=2, keepdims=True)
+
+
+@pytest.mark.parametrize("prec", [L.PREC_FP32, L.PREC_BF16X3_REF])
+def test_field_terms(ctx, small, headmap, prec):
+    mesh, mats, ops, mid = small
+    hm, hid = headmap
+    B = 100                                     # not a multiple of the 128-row tile
+    isl = synth.jittered_islands(B, seed=21, mesh_id=mid)
+    isl.Hext_T[:] = np.array([0.01, -0.02, 0.03], np.float32)
+    p = synth.RunParams(dt_ps=0.1, substeps=1, alpha=0.1, rise_ps=80.0, use_map=True,
+                        uniform_T=synth.uniform_field(0.4, 160.0))
+    m = _smooth_state(ops.xyz, B, 3)
+    ob = llg.Batch(ops, isl, p, head_map=hm)
+    with ctx.batch(isl, p, precision=prec, map_id=hid) as bt:
+        bt.set_state(m.transpose(0, 2, 1).astype(np.float32), 0.0)
+        mf = bt.read()["m"].transpose(0, 2, 1).astype(np.float64)
+        t = 37.5
+        tol = {L.TERM_EXCHANGE: 2e-6, L.TERM_ANISOTROPY: 2e-6, L.TERM_HEAD: 2e-6, L.TERM_UNIFORM: 2e-6,
+               L.TERM_DEMAG: 2e-6 if prec == L.PREC_FP32 else 2e-5}
+        for term, rel in tol.items():
+            g = bt.field(t, term).transpose(0, 2, 1)
+            o = ob.field(mf, t, term)
+            scale = max(np.abs(o).max(), 1e-3)
+            err = np.abs(g - o).max()
+            print(f"prec {prec} term {term}: max err {err:.3e} scale {scale:.3e}")
+            assert err <= rel * scale * 10, (term, err, scale)
+
+
+def _traj_parity(ctx, ops, mid, hm, hid, isl, p, prec, every, n_samples):
+    ob = llg.Batch(ops, isl, p, head_map=hm)
+    ref = ob.run(sample_every=every)
+    worst = 0.0
+    with ctx.batch(isl, p, precision=prec, map_id=hid) as bt:
+        for s in range(n_samples):
+            bt.advance(every)
+            g = bt.read()["m"].transpose(0, 2, 1)
+            worst = max(worst, float(np.abs(g - ref["samples"][s]).max()))
+        out = bt.read()
+    return worst, ref, out
+
+
+@pytest.mark.parametrize("prec", [L.PREC_FP32, L.PREC_BF16X3_REF])
+def test_dynamics_parity_first_100ps(ctx, small, headmap, prec):
+    mesh, mats, ops, mid = small
+    hm, hid = headmap
+    B = 40
+    isl = synth.jittered_islands(B, seed=31, mesh_id=mid)
+    isl.pos_nm[:, 0] += 6.0                     # under the head centre mid-run
+    p = synth.RunParams(dt_ps=0.1, t_end_ps=100.0, alpha=0.1, rise_ps=50.0, use_map=True, v_m_per_s=20.0,
+                        x0_nm=-4.0, uniform_T=synth.uniform_field(0.5, 170.0))
+    p.substeps = llg.stable_substeps(llg.Batch(ops, isl, p, head_map=hm))
+    worst, ref, out = _traj_parity(ctx, ops, mid, hm, hid, isl, p, prec, every=20, n_samples=50)
+    assert worst <= 1e-3, worst
+    assert np.all(out["status"] == 0)
+    assert np.abs(np.linalg.norm(out["m"], axis=1) - 1.0).max() < 1e-5
+
+
+def test_switching_outcomes_and_times(ctx, small):
+    mesh, mats, ops, mid = small
+    B = 64
+    isl = synth.jittered_islands(B, seed=41, mesh_id=mid)
+    Bmag = 0.81
+    isl.Hext_T[:] = np.array([math.sin(math.radians(170)) * Bmag, 0.0, math.cos(math.radians(170)) * Bmag],
+                             np.float32)
+    p = synth.RunParams(dt_ps=0.1, t_end_ps=200.0, alpha=0.1, rise_ps=0.0, use_map=False)
+    ob = llg.Batch(ops, isl, p)
+    p.substeps = llg.stable_substeps(ob)
+    ref = ob.run()
+    assert 0 < ref["switched"].sum() < B            # a mix of outcomes
+    for prec in (L.PREC_FP32, L.PREC_BF16X3_REF):
+        out = ctx.run_batch(isl, p, p.n_intervals, precision=prec)
+        assert np.array_equal(out["switched"], ref["switched"]), prec
+        sw = ref["t_sw"] > 0
+        assert np.array_equal(out["t_sw"] > 0, sw)
+        assert np.abs(out["t_sw"][sw] - ref["t_sw"][sw]).max() <= 2.0
+
+
+def test_census_size_sampled_islands(ctx, headmap):
+    # the full-size workload shape (4096 islands, ~1500-node mesh, head map); the
+    # oracle recomputes a sample of islands one by one
+    hm, hid = headmap
+    mesh = synth.census_island_mesh()
+    mats = synth.ecc_materials()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    mid = ctx.mesh_upload(mesh, mats)
+    B = 4096
+    isl = synth.jittered_islands(B, seed=1, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, t_end_ps=1.0, alpha=0.1, rise_ps=100.0, use_map=True, x0_nm=-2.0)
+    p.substeps = api.stable_substeps(api.field_bound(ctx, mid, isl, p, hm), p.dt_ps, p.alpha)
+    assert p.substeps == llg.stable_substeps(llg.Batch(ops, isl.subset(np.arange(B)), p, head_map=hm))
+    out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_FP32, map_id=hid)
+    assert np.all(out["status"] == 0)
+    assert np.abs(np.linalg.norm(out["m"], axis=1) - 1.0).max() < 1e-5
+    pick = np.array([0, 1234, 2047, 4095])
+    ob = llg.Batch(ops, isl.subset(pick), p, head_map=hm)
+    ref = ob.run()
+    assert np.abs(out["m"][pick].transpose(0, 2, 1) - ref["m"]).max() <= 1e-3
