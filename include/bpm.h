@@ -213,6 +213,38 @@ int bpm_run_batch(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_
                   int32_t n_intervals, float* m_final, int32_t ld, uint8_t* switched,
                   float* t_sw_ps, int32_t* status);
 
+/* Size of the fixed device scratch array used by bpm_llg_advance_noalloc. */
+#define BPM_NOALLOC_SCRATCH_BYTES (8 * 1024 * 1024)
+
+/* Allocation-free advance.  The paper has no counterpart to this entry point;
+ * it exists for callers that cannot allocate device memory when they step
+ * islands -- for example a host application whose own pool allocator has
+ * reserved the device memory, or a time-critical loop that must not stall on
+ * cudaMalloc/cudaFree (which can synchronise the device).  It performs the
+ * same FP32 batch advance as a BPM_PREC_FP32 batch (same kernels, same
+ * arithmetic) but allocates nothing: its scratch (island table, Heun stages,
+ * demag operand and field, switch-detector state, step counter) lives in one
+ * fixed device array of BPM_NOALLOC_SCRATCH_BYTES bytes that every GPU which
+ * loads the library holds until the process exits.
+ *   isl, B      host island table, one mesh for all islands
+ *   p           run parameters; p->precision must be BPM_PREC_FP32; the run
+ *               starts at p->t0_ps with the switch detector reset
+ *   m           device [B][3][ld]: the state at p->t0_ps on entry, the state
+ *               after n_intervals intervals on return (stream-ordered)
+ *   mz          device [B] volume-averaged m_z at the end, or NULL
+ * Requests whose scratch would exceed the array (about 60*B*n_pad bytes, e.g.
+ * 80 islands of a 1547-node mesh) fail with BPM_ERR_ARG and a message giving
+ * the size needed.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array, which keeps the previous call's
+ * contents (each call clears the region it uses): calls that overlap on the
+ * GPU -- on different streams or contexts of the same device -- race and
+ * corrupt each other.  Work is ordered on the context's stream; the call does
+ * not synchronise. */
+int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int32_t B,
+                            const bpm_run_params* p, int32_t n_intervals, float* m, int32_t ld,
+                            float* mz);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,11 @@ PROTOTYPES = {
     "bpm_batch_destroy": (c_int, [c_void_p]),
     "bpm_run_batch": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,
                               c_void_p, c_void_p, c_void_p]),
+    "bpm_llg_advance_noalloc": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p,
+                                        c_int32, c_void_p]),
 }
+
+NOALLOC_SCRATCH_BYTES = 8 * 1024 * 1024
 
 _lib = None
 

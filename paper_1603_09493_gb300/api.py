@@ -124,6 +124,14 @@ class Context:
                                        L.ptr(sw), L.ptr(tsw), L.ptr(st)))
         return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st)
 
+    def llg_advance_noalloc(self, islands, params, n_intervals, m_dev, mz_dev=None, map_id=-1):
+        """FP32 advance with no device allocation (bpm_llg_advance_noalloc):
+        m_dev is a device tensor [B][3][ld] updated in place on the context stream."""
+        isl = island_array(islands)
+        q = run_params(params, L.PREC_FP32, map_id)
+        L.check(self.lib.bpm_llg_advance_noalloc(self.h, L.ptr(isl), len(isl), byref(q), int(n_intervals),
+                                                 L.ptr(m_dev), int(m_dev.shape[-1]), L.ptr(mz_dev)))
+
 
 class Batch:
     def __init__(self, ctx: Context, islands, params, precision, map_id):
