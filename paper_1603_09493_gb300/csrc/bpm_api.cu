@@ -543,10 +543,16 @@ int bpm_batch_read(bpm_batch* bt, float* m, int32_t ld, uint8_t* switched, float
     }
     std::vector<float> mzv(B), tsw(B);
     std::vector<int> st(B);
+    int gerr = 0;
+    BPM_CK(cudaMemcpyAsync(&gerr, bt->gemm_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     BPM_CK(cudaMemcpyAsync(mzv.data(), bt->mz_prev, B * sizeof(float), cudaMemcpyDeviceToHost, s));
     BPM_CK(cudaMemcpyAsync(tsw.data(), bt->t_sw, B * sizeof(float), cudaMemcpyDeviceToHost, s));
     BPM_CK(cudaMemcpyAsync(st.data(), bt->status, B * sizeof(int), cudaMemcpyDeviceToHost, s));
     BPM_CK(cudaStreamSynchronize(s));
+    if (gerr) {
+        set_error("a bounded wait in the tensor-core demag GEMM gave up (code %d); results are invalid", gerr);
+        return BPM_ERR_TIMEOUT;
+    }
     for (int b = 0; b < B; ++b) {
         if (switched) switched[b] = mzv[b] <= 0.f ? 1 : 0;
         if (t_sw_ps) t_sw_ps[b] = tsw[b];

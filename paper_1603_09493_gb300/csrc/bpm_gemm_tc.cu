@@ -1,12 +1,338 @@
-// tcgen05 BF16 split demag GEMM (placeholder until the tensor-core kernel lands).
+// Demag GEMM on the 5th-generation tensor cores (tcgen05, sm_103a):
+//   C[M][N] = sum over products of A_x[M][K] * W_y[N][K]^T,  FP32 accumulate in TMEM,
+// with the BF16 hi/lo split of both operands:
+//   products = 3: Ahi*Whi + Alo*Whi + Ahi*Wlo   (the lo*lo term, ~2^-16 relative, is dropped)
+//   products = 1: Ahi*Whi
+// A is the demag source Ms*m of the batch ([M] islands x [K] = 3 n_pad, K-major), W the
+// demag operator (row = output node/component, K-major).
+//
+// One CTA computes a 128 x 256 output tile.  Warp 0 (one elected lane) streams the
+// k-blocks (64 BF16 = one 128-byte swizzle atom) of every operand tile with TMA into a
+// ring of shared-memory stages, warp 1 (one elected lane) issues the tcgen05.mma
+// instructions into a 128-lane x 256-column TMEM accumulator, and after the last
+// k-block all four warps read the accumulator back with tcgen05.ld and store it.
+// Each stage holds Ahi, Alo, Whi, Wlo for one k-block, so the three products of a
+// k-block share the staged tiles.  Every mbarrier wait is bounded; on timeout the
+// kernel records an error flag, drains its own copies and MMAs, frees TMEM and exits.
+#include <cuda.h>
+
 #include "bpm_internal.cuh"
 
 namespace bpm {
 
-int gemm_bf16x3_tc(cudaStream_t, int, int, int, const __nv_bfloat16*, const __nv_bfloat16*,
-                   const __nv_bfloat16*, const __nv_bfloat16*, float*, int, int*, int) {
-    set_error("tensor-core demag GEMM not built in this version");
-    return BPM_ERR_STATE;
+namespace {
+
+constexpr int TM = 128, TN = 256, TK = 64;                  // tile, TK = one 128 B swizzle row of BF16
+constexpr int A_TILE = TM * TK * 2, W_TILE = TN * TK * 2;    // 16 KB, 32 KB
+constexpr unsigned long long kWaitNs = 200000000ull;      // 200 ms per wait (a normal wait is < 0.1 ms)
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait: returns false (and raises the error flag) if the phase does not complete
+// within kWaitNs, or as soon as another CTA has raised the flag
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs || *(volatile int*)err != 0) break;
+    }
+    atomicExch(err, code);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand tile written by TMA with 128 B swizzle
+// (rows of 128 B, 8-row groups 1024 B apart); start address advances 32 B per K=16 slice
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);       // start address
+    d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                        // 128 B swizzle
+    return d;
+}
+
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128, N = 256
+constexpr uint32_t kIdesc = (1u << 4)              // D = F32
+                            | (1u << 7)            // A = BF16
+                            | (1u << 10)           // B = BF16
+                            | ((uint32_t)(TN >> 3) << 17)
+                            | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int P>
+struct Cfg {
+    static constexpr int stage_bytes = (P == 3 ? 2 : 1) * (A_TILE + W_TILE);
+    static constexpr int stages = (P == 3) ? 2 : 4;
+    static constexpr int smem = stages * stage_bytes + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+              const __grid_constant__ CUtensorMap mWhi, const __grid_constant__ CUtensorMap mWlo, int M, int N, int K,
+              float* __restrict__ C, int* err) {
+    using CF = Cfg<P>;
+    constexpr int S = CF::stages;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;             // 1024 B alignment for the swizzle atoms
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t bar0 = base + S * CF::stage_bytes;         // full[S], empty[S], done, tmem slot
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+    const uint32_t done_bar = bar0 + 8u * (2 * S);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * CF::stage_bytes + 8 * (2 * S + 1));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * TN, m0 = blockIdx.y * TM;
+    const int nk = K / TK;
+    if (*(volatile int*)err != 0) return;      // an earlier launch gave up: results are invalid anyway
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    auto sAhi = [&](int s) { return base + s * CF::stage_bytes; };
+    auto sWhi = [&](int s) { return base + s * CF::stage_bytes + A_TILE; };
+    auto sAlo = [&](int s) { return base + s * CF::stage_bytes + A_TILE + W_TILE; };
+    auto sWlo = [&](int s) { return base + s * CF::stage_bytes + 2 * A_TILE + W_TILE; };
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int issued = 0;
+        bool ok = true;
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int s = kb % S;
+            if (kb >= S) ok = mbar_wait(empty_bar(s), ((kb / S) - 1) & 1, err, 1);
+            if (!ok) break;
+            mbar_expect_tx(full_bar(s), CF::stage_bytes);
+            const int kc = kb * TK;
+            tma_load_2d(sAhi(s), &mAhi, kc, m0, full_bar(s));
+            tma_load_2d(sWhi(s), &mWhi, kc, n0, full_bar(s));
+            if (P == 3) {
+                tma_load_2d(sAlo(s), &mAlo, kc, m0, full_bar(s));
+                tma_load_2d(sWlo(s), &mWlo, kc, n0, full_bar(s));
+            }
+            issued = kb + 1;
+        }
+        // drain: every stage armed so far must have landed before the CTA may exit
+        for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
+            mbar_wait(full_bar(kb % S), (kb / S) & 1, err, 2);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        bool ok = true;
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int s = kb % S;
+            ok = mbar_wait(full_bar(s), (kb / S) & 1, err, 3);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int k = 0; k < TK / 16; ++k) {
+                const uint32_t koff = 32u * k;
+                const uint64_t ahi = sw128_desc(sAhi(s) + koff), whi = sw128_desc(sWhi(s) + koff);
+                mma_bf16(tmem, ahi, whi, (kb > 0 || k > 0) ? 1u : 0u);
+                if (P == 3) {
+                    const uint64_t alo = sw128_desc(sAlo(s) + koff), wlo = sw128_desc(sWlo(s) + koff);
+                    mma_bf16(tmem, alo, whi, 1u);
+                    mma_bf16(tmem, ahi, wlo, 1u);
+                }
+            }
+            mma_commit(empty_bar(s));
+        }
+        mma_commit(done_bar);       // tracks every MMA issued above, also on the error path
+    }
+    __syncwarp();
+    // ---------------- epilogue: TMEM -> registers -> global ----------------
+    const bool have = mbar_wait(done_bar, 0, err, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // tcgen05.ld is warp-collective: take the decision once per warp
+    const int go = __shfl_sync(0xffffffffu, (have && *(volatile int*)err == 0) ? 1 : 0, 0);
+    if (go) {
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < TN; c += 32) {
+            uint32_t r[32];
+            tmem_ld32(lane_addr + (uint32_t)c, r);
+            const int col = n0 + c;
+            if (row < M && col < N) {
+                float4* dst = reinterpret_cast<float4*>(C + (size_t)row * N + col);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (col + 4 * q < N)
+                        dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                             __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+int make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return BPM_ERR_CUDA;
+    }
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15u) || (inner % 8)) {
+        set_error("TMA operand not 16-byte aligned (ptr %p, inner %d)", ptr, inner);
+        return BPM_ERR_ARG;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return BPM_ERR_CUDA;
+    }
+    return BPM_OK;
+}
+
+template <int P>
+int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
+           const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, float* C, int* err) {
+    static bool configured = false;
+    if (!configured) {
+        BPM_CK(cudaFuncSetAttribute(k_gemm_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<P>::smem));
+        configured = true;
+    }
+    CUtensorMap mAhi, mAlo, mWhi, mWlo;
+    BPM_TRY(make_map(&mAhi, Ahi, K, M, TM));
+    BPM_TRY(make_map(&mWhi, Whi, K, N, TN));
+    if (P == 3) {
+        BPM_TRY(make_map(&mAlo, Alo, K, M, TM));
+        BPM_TRY(make_map(&mWlo, Wlo, K, N, TN));
+    } else {
+        mAlo = mAhi;
+        mWlo = mWhi;
+    }
+    dim3 grid((N + TN - 1) / TN, M / TM);
+    k_gemm_tc<P><<<grid, kThreads, Cfg<P>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, C, err);
+    BPM_CK(cudaGetLastError());
+    return BPM_OK;
+}
+
+}  // namespace
+
+int gemm_bf16x3_tc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
+                   const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, float* C, int products, int* err_flag,
+                   int /*sm_count*/) {
+    if (M % TM || K % TK || N % 16 || M <= 0 || N <= 0) {
+        set_error("tensor-core GEMM needs M %% %d == 0, K %% %d == 0, N %% 16 == 0 (M=%d N=%d K=%d)", TM, TK, M, N, K);
+        return BPM_ERR_ARG;
+    }
+    if (products == 3) return launch<3>(s, M, N, K, Ahi, Alo, Whi, Wlo, C, err_flag);
+    if (products == 1) return launch<1>(s, M, N, K, Ahi, Alo, Whi, Wlo, C, err_flag);
+    set_error("products must be 1 or 3");
+    return BPM_ERR_ARG;
 }
 
 }  // namespace bpm

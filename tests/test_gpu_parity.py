@@ -95,7 +95,7 @@ def _smooth_state(xyz, B, seed):
     return m / np.linalg.norm(m, axis=2, keepdims=True)
 
 
-@pytest.mark.parametrize("prec", [L.PREC_FP32, L.PREC_BF16X3_REF])
+@pytest.mark.parametrize("prec", [L.PREC_FP32, L.PREC_BF16X3_REF, L.PREC_BF16X3])
 def test_field_terms(ctx, small, headmap, prec):
     mesh, mats, ops, mid = small
     hm, hid = headmap
@@ -134,7 +134,7 @@ def _traj_parity(ctx, ops, mid, hm, hid, isl, p, prec, every, n_samples):
     return worst, ref, out
 
 
-@pytest.mark.parametrize("prec", [L.PREC_FP32, L.PREC_BF16X3_REF])
+@pytest.mark.parametrize("prec", [L.PREC_FP32, L.PREC_BF16X3_REF, L.PREC_BF16X3])
 def test_dynamics_parity_first_100ps(ctx, small, headmap, prec):
     mesh, mats, ops, mid = small
     hm, hid = headmap
@@ -162,7 +162,7 @@ def test_switching_outcomes_and_times(ctx, small):
     p.substeps = llg.stable_substeps(ob)
     ref = ob.run()
     assert 0 < ref["switched"].sum() < B            # a mix of outcomes
-    for prec in (L.PREC_FP32, L.PREC_BF16X3_REF):
+    for prec in (L.PREC_FP32, L.PREC_BF16X3):
         out = ctx.run_batch(isl, p, p.n_intervals, precision=prec)
         assert np.array_equal(out["switched"], ref["switched"]), prec
         sw = ref["t_sw"] > 0
@@ -183,7 +183,7 @@ def test_census_size_sampled_islands(ctx, headmap):
     p = synth.RunParams(dt_ps=0.1, t_end_ps=1.0, alpha=0.1, rise_ps=100.0, use_map=True, x0_nm=-2.0)
     p.substeps = api.stable_substeps(api.field_bound(ctx, mid, isl, p, hm), p.dt_ps, p.alpha)
     assert p.substeps == llg.stable_substeps(llg.Batch(ops, isl.subset(np.arange(B)), p, head_map=hm))
-    out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_FP32, map_id=hid)
+    out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_BF16X3, map_id=hid)
     assert np.all(out["status"] == 0)
     assert np.abs(np.linalg.norm(out["m"], axis=1) - 1.0).max() < 1e-5
     pick = np.array([0, 1234, 2047, 4095])

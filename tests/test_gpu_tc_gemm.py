@@ -1,0 +1,74 @@
+"""The tcgen05 demag GEMM against the CUDA-core evaluation of the same BF16
+split products and against FP32, through the demag term of bpm_batch_field.
+
+Same products, different summation: the tensor core adds each MMA's products
+into the FP32 accumulator with its own alignment and rounding, not as a chain
+of IEEE FMAs.  Bound: one relative rounding of 2^-23 of the accumulator per MMA
+issue, (3 K / 16) * 2^-23 of the field scale (2.1e-5 at K = 960, 1.1e-4 at
+K = 4800; measured 3.2e-6 and 1.6e-5).  Against FP32 the split operands add
+~2^-17 relative each.  One BF16 product: ~2^-9 per operand (measured ~3e-3,
+bound 2e-2)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1603_09493_gb300 import _lib as L
+from paper_1603_09493_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not os.path.exists(L.LIB_PATH):
+        from paper_1603_09493_gb300 import build
+        build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _state(xyz, B, seed):
+    rng = np.random.default_rng(seed)
+    m = rng.standard_normal((B, 3, xyz.shape[0])) * 0.3
+    m[:, 2, :] += 1.0
+    return (m / np.linalg.norm(m, axis=1, keepdims=True)).astype(np.float32)
+
+
+def _demag(ctx, isl, p, prec, m):
+    with ctx.batch(isl, p, precision=prec) as bt:
+        bt.set_state(m, 0.0)
+        return bt.field(0.0, L.TERM_DEMAG)
+
+
+@pytest.mark.parametrize("case", ["ragged_small", "census"])
+def test_tc_gemm_matches_split_reference_and_fp32(ctx, case):
+    if case == "ragged_small":
+        mesh = synth.layered_island_mesh(8.0, 7.0, 3.0, rings=2, hard_slabs=10, soft_slabs=5, seed=4)
+        B = 200                           # two 128-row tiles, second one partly padding
+    else:
+        mesh = synth.census_island_mesh()
+        B = 4096
+    mid = ctx.mesh_upload(mesh, synth.ecc_materials())
+    info = ctx.mesh_info(mid)
+    if case == "ragged_small":
+        assert (3 * info["n_pad"]) % 256 != 0
+    isl = synth.jittered_islands(B, seed=3, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, substeps=1, term_mask=L.TERM_DEMAG)
+    m = _state(mesh.xyz_nm, B, 5)
+    f32 = _demag(ctx, isl, p, L.PREC_FP32, m)
+    ref = _demag(ctx, isl, p, L.PREC_BF16X3_REF, m)
+    tc3 = _demag(ctx, isl, p, L.PREC_BF16X3, m)
+    tc1 = _demag(ctx, isl, p, L.PREC_BF16, m)
+    scale = np.abs(f32).max()
+    K = 3 * info["n_pad"]
+    acc_bound = (3 * K / 16) * 2.0 ** -23
+    e_ref = np.abs(tc3 - ref).max() / scale
+    e_f32 = np.abs(tc3 - f32).max() / scale
+    e_1 = np.abs(tc1 - f32).max() / scale
+    print(f"{case}: |tc3-ref| {e_ref:.2e}  |tc3-f32| {e_f32:.2e}  |tc1-f32| {e_1:.2e}  scale {scale:.3f} T")
+    assert np.all(np.isfinite(tc3)) and np.all(np.isfinite(tc1))
+    assert e_ref <= acc_bound
+    assert e_f32 <= acc_bound + 4 * 2.0 ** -17
+    assert e_1 <= 2e-2
