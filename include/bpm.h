@@ -213,6 +213,50 @@ int bpm_run_batch(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_
                   int32_t n_intervals, float* m_final, int32_t ld, uint8_t* switched,
                   float* t_sw_ps, int32_t* status);
 
+/* ---------------------------------------------------------------------- */
+/* Surrogate MLP (stands in for the Gaussian-process predictor of the      */
+/* efficient global optimisation, Sec. II.A)                               */
+/* ---------------------------------------------------------------------- */
+
+/* x[n_in] -> (Linear -> GELU) x depth (width wide) -> Linear -> n_out logits. */
+typedef struct {
+    int32_t n_in, width, depth, n_out;   /* e.g. 16, 256, 4, 2 */
+} bpm_mlp_cfg;
+
+/* AdamW with decoupled weight decay on the weight matrices only. */
+typedef struct {
+    int32_t epochs, batch;
+    float   lr, weight_decay, beta1, beta2, eps;
+    int32_t pad_;
+} bpm_train_cfg;
+
+/* Flat parameter layout shared by create / get / grad: for each layer l in
+ * order, W_l [out][in] row-major, then b_l [out]. */
+
+/* Create a surrogate with the given initial parameters (host, float32 [P]).
+ * Training and inference run every contraction on the tensor cores with BF16
+ * weights/activations and FP32 accumulation; FP32 master weights and the Adam
+ * moments stay on the device. */
+int bpm_surrogate_create(bpm_ctx* ctx, const bpm_mlp_cfg* cfg, const float* params, int32_t* sid);
+int bpm_surrogate_param_count(bpm_ctx* ctx, int32_t sid, int64_t* count);
+int bpm_surrogate_get_params(bpm_ctx* ctx, int32_t sid, float* out);
+/* Mean sigmoid-BCE loss and its gradient (flat layout) on one batch X [N][n_in],
+ * Y [N][n_out] (host); no parameter update. */
+int bpm_surrogate_grad(bpm_ctx* ctx, int32_t sid, const float* X, const float* Y, int32_t N, float* grad,
+                       float* loss);
+/* Train: `epochs` passes over X, Y (host) in the given sample order, minibatches
+ * of cfg->batch (the last one partial), one AdamW step per minibatch.
+ * loss_curve: host [epochs * ceil(N/batch)] or NULL. */
+int bpm_surrogate_train(bpm_ctx* ctx, int32_t sid, const float* X, const float* Y, int64_t N,
+                        const bpm_train_cfg* cfg, float* loss_curve);
+/* Probabilities sigmoid(logits) P [N][n_out] for X [N][n_in] (both host, or both
+ * device if on_device, stream-ordered). */
+int bpm_surrogate_infer(bpm_ctx* ctx, int32_t sid, const float* X, int64_t N, float* P, int on_device);
+/* Checkpoint of weights, Adam moments and step count; load needs the same shape. */
+int bpm_surrogate_save(bpm_ctx* ctx, int32_t sid, const char* path);
+int bpm_surrogate_load(bpm_ctx* ctx, int32_t sid, const char* path);
+int bpm_surrogate_destroy(bpm_ctx* ctx, int32_t sid);
+
 /* Size of the fixed device scratch array used by bpm_llg_advance_noalloc. */
 #define BPM_NOALLOC_SCRATCH_BYTES (8 * 1024 * 1024)
 

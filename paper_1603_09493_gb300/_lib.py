@@ -3,7 +3,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int32, c_uint8, c_uint32, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_int32, c_int64, c_uint8, c_uint32, c_void_p
 
 import numpy as np
 
@@ -47,6 +47,15 @@ class bpm_mesh_info(ctypes.Structure):
                 ("cg_residual_dirichlet", c_double)]
 
 
+class bpm_mlp_cfg(ctypes.Structure):
+    _fields_ = [("n_in", c_int32), ("width", c_int32), ("depth", c_int32), ("n_out", c_int32)]
+
+
+class bpm_train_cfg(ctypes.Structure):
+    _fields_ = [("epochs", c_int32), ("batch", c_int32), ("lr", c_float), ("weight_decay", c_float),
+                ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("pad_", c_int32)]
+
+
 # name -> (restype, argtypes); every function declared in include/bpm.h
 PROTOTYPES = {
     "bpm_create": (c_int, [POINTER(c_void_p), c_int, c_void_p]),
@@ -70,6 +79,16 @@ PROTOTYPES = {
     "bpm_batch_destroy": (c_int, [c_void_p]),
     "bpm_run_batch": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,
                               c_void_p, c_void_p, c_void_p]),
+    "bpm_surrogate_create": (c_int, [c_void_p, POINTER(bpm_mlp_cfg), c_void_p, POINTER(c_int32)]),
+    "bpm_surrogate_param_count": (c_int, [c_void_p, c_int32, POINTER(c_int64)]),
+    "bpm_surrogate_get_params": (c_int, [c_void_p, c_int32, c_void_p]),
+    "bpm_surrogate_grad": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "bpm_surrogate_train": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_int64, POINTER(bpm_train_cfg),
+                                    c_void_p]),
+    "bpm_surrogate_infer": (c_int, [c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_int]),
+    "bpm_surrogate_save": (c_int, [c_void_p, c_int32, c_char_p]),
+    "bpm_surrogate_load": (c_int, [c_void_p, c_int32, c_char_p]),
+    "bpm_surrogate_destroy": (c_int, [c_void_p, c_int32]),
     "bpm_llg_advance_noalloc": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p,
                                         c_int32, c_void_p]),
 }

@@ -132,6 +132,74 @@ class Context:
         L.check(self.lib.bpm_llg_advance_noalloc(self.h, L.ptr(isl), len(isl), byref(q), int(n_intervals),
                                                  L.ptr(m_dev), int(m_dev.shape[-1]), L.ptr(mz_dev)))
 
+    def surrogate(self, sizes, params) -> "Surrogate":
+        return Surrogate(self, sizes, params)
+
+
+class Surrogate:
+    """Handle of a device-resident MLP surrogate (bpm_surrogate_*)."""
+
+    def __init__(self, ctx: Context, sizes, params):
+        n_in, width, depth, n_out = sizes
+        self.ctx, self.lib = ctx, ctx.lib
+        self.n_in, self.n_out = n_in, n_out
+        cfg = L.bpm_mlp_cfg(n_in, width, depth, n_out)
+        flat = np.ascontiguousarray(params, np.float32)
+        sid = c_int32()
+        L.check(self.lib.bpm_surrogate_create(ctx.h, byref(cfg), L.ptr(flat), byref(sid)))
+        self.sid = sid.value
+        cnt = ctypes.c_int64()
+        L.check(self.lib.bpm_surrogate_param_count(ctx.h, self.sid, byref(cnt)))
+        self.P = cnt.value
+        if flat.size != self.P:
+            raise ValueError(f"expected {self.P} parameters, got {flat.size}")
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.P, np.float32)
+        L.check(self.lib.bpm_surrogate_get_params(self.ctx.h, self.sid, L.ptr(out)))
+        return out
+
+    def grad(self, X, Y):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        g = np.zeros(self.P, np.float32)
+        loss = ctypes.c_float()
+        L.check(self.lib.bpm_surrogate_grad(self.ctx.h, self.sid, L.ptr(X), L.ptr(Y), X.shape[0], L.ptr(g),
+                                            byref(loss)))
+        return g, loss.value
+
+    def train(self, X, Y, epochs, batch, lr, weight_decay, beta1=0.9, beta2=0.999, eps=1e-8):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        cfg = L.bpm_train_cfg(int(epochs), int(batch), lr, weight_decay, beta1, beta2, eps, 0)
+        steps = int(epochs) * ((X.shape[0] + int(batch) - 1) // int(batch))
+        curve = np.zeros(steps, np.float32)
+        L.check(self.lib.bpm_surrogate_train(self.ctx.h, self.sid, L.ptr(X), L.ptr(Y), X.shape[0], byref(cfg),
+                                             L.ptr(curve)))
+        return curve
+
+    def infer(self, X) -> np.ndarray:
+        on_dev = int(hasattr(X, "data_ptr"))
+        if on_dev:
+            import torch
+            P = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        else:
+            X = np.ascontiguousarray(X, np.float32)
+            P = np.zeros((X.shape[0], self.n_out), np.float32)
+        L.check(self.lib.bpm_surrogate_infer(self.ctx.h, self.sid, L.ptr(X), X.shape[0], L.ptr(P), on_dev))
+        return P
+
+    def save(self, path: str):
+        L.check(self.lib.bpm_surrogate_save(self.ctx.h, self.sid, path.encode()))
+
+    def load(self, path: str):
+        L.check(self.lib.bpm_surrogate_load(self.ctx.h, self.sid, path.encode()))
+
+    def destroy(self):
+        if self.sid is not None:
+            self.lib.bpm_surrogate_destroy(self.ctx.h, self.sid)
+            self.sid = None
+
 
 class Batch:
     def __init__(self, ctx: Context, islands, params, precision, map_id):

@@ -175,6 +175,7 @@ void bpm_destroy(bpm_ctx* ctx) {
     for (bpm_batch* b : live_batches(ctx)) free_batch(b);
     live_batches(ctx).clear();
     for (Mesh* m : ctx->meshes) free_mesh(m);
+    for (Mlp* m : ctx->mlps) free_mlp(m);
     for (HeadMap* h : ctx->maps) {
         if (h) cudaFree(h->B);
         delete h;

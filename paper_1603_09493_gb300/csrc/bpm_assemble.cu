@@ -847,6 +847,7 @@ int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets_
     for (int i = 0; i < n; ++i) {
         pos[i] = make_float4((float)xyz[3 * i], (float)xyz[3 * i + 1], (float)xyz[3 * i + 2],
                              (float)(M->V[i] / Vsum));
+
         double an = 2.0 * M->Ku[i] / M->Ms[i];
         nm[i] = make_float4((float)an, (float)(M->Ms[i] * 1e-6), 0.f, 0.f);
         an_max = std::max(an_max, an);

@@ -134,11 +134,72 @@ struct Cfg {
     static constexpr int smem = stages * stage_bytes + 1024 /*align*/ + 256 /*barriers*/;
 };
 
-template <int P>
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// Epilogue of one thread: row `row`, 32 accumulator columns starting at `col`.
+template <int EPI>
+__device__ __forceinline__ void epilogue32(const TcEpilogue& e, int M, int N, int row, int col, const uint32_t (&r)[32],
+                                           float (&colsum)[32]) {
+    const bool rok = row < M && row < e.rows_valid;
+    if (EPI == TC_EPI_STORE) {
+        if (!rok || col >= N) return;
+        if (e.cols_valid >= N && (e.ldc % 4) == 0) {
+            float4* dst = reinterpret_cast<float4*>(e.C + (size_t)row * e.ldc + col);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (col + 4 * q < N)
+                    dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                         __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (col + q < e.cols_valid) e.C[(size_t)row * e.ldc + col + q] = __uint_as_float(r[q]);
+        }
+    } else if (EPI == TC_EPI_BIAS_GELU) {
+        // z = acc + b; keep z (for the backward pass) and h = GELU(z) in both layouts
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int c = col + q;
+            if (c >= N) break;
+            const float z = __uint_as_float(r[q]) + (c < e.cols_valid ? e.bias[c] : 0.f);
+            const float h = (c < e.cols_valid) ? gelu(z) : 0.f;
+            // rows past the valid batch are written as zeros so that no stale value travels on
+            if (e.C && rok) e.C[(size_t)row * e.ldc + c] = z;
+            if (row < M) e.H[(size_t)row * e.ldh + c] = __float2bfloat16_rn(rok ? h : 0.f);
+            if (e.HT && row < M) e.HT[(size_t)c * e.ldht + row] = __float2bfloat16_rn(rok ? h : 0.f);
+        }
+    } else if (EPI == TC_EPI_BIAS_OUT) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int c = col + q;
+            if (!rok || c >= e.cols_valid) break;
+            const float z = __uint_as_float(r[q]) + e.bias[c];
+            e.C[(size_t)row * e.ldc + c] = e.sigmoid ? 1.f / (1.f + expf(-z)) : z;
+        }
+    } else if (EPI == TC_EPI_GELU_BWD) {
+        // dz = dh * GELU'(z) in both layouts, plus per-column sums for the bias gradient
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int c = col + q;
+            float dz = 0.f;
+            if (rok && c < e.cols_valid) dz = __uint_as_float(r[q]) * gelu_grad(e.Zin[(size_t)row * e.ldz + c]);
+            colsum[q] = dz;
+            if (c < N) {
+                if (row < M) e.H[(size_t)row * e.ldh + c] = __float2bfloat16_rn(dz);
+                if (e.HT && row < M) e.HT[(size_t)c * e.ldht + row] = __float2bfloat16_rn(dz);
+            }
+        }
+    }
+}
+
+template <int P, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
               const __grid_constant__ CUtensorMap mWhi, const __grid_constant__ CUtensorMap mWlo, int M, int N, int K,
-              float* __restrict__ C, int* err) {
+              const TcEpilogue e, int* err) {
     using CF = Cfg<P>;
     constexpr int S = CF::stages;
     extern __shared__ uint8_t smem_raw[];
@@ -236,15 +297,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int c = 0; c < TN; c += 32) {
             uint32_t r[32];
+            float colsum[32];
             tmem_ld32(lane_addr + (uint32_t)c, r);
             const int col = n0 + c;
-            if (row < M && col < N) {
-                float4* dst = reinterpret_cast<float4*>(C + (size_t)row * N + col);
+            epilogue32<EPI>(e, M, N, row, col, r, colsum);
+            if (EPI == TC_EPI_GELU_BWD && e.colsum && col < N) {
+                // fixed-order warp sums -> one partial per (row block of 32, column)
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (col + 4 * q < N)
-                        dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                             __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                for (int q = 0; q < 32; ++q) {
+                    float v = colsum[q];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == q && col + q < N)
+                        e.colsum[(size_t)(blockIdx.y * 4 + warp) * e.ldcs + col + q] = v;
+                }
             }
         }
     }
@@ -296,12 +361,12 @@ int make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_row
     return BPM_OK;
 }
 
-template <int P>
+template <int P, int EPI>
 int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
-           const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, float* C, int* err) {
+           const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, const TcEpilogue& e, int* err) {
     static bool configured = false;
     if (!configured) {
-        BPM_CK(cudaFuncSetAttribute(k_gemm_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<P>::smem));
+        BPM_CK(cudaFuncSetAttribute(k_gemm_tc<P, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<P>::smem));
         configured = true;
     }
     CUtensorMap mAhi, mAlo, mWhi, mWlo;
@@ -315,7 +380,7 @@ int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const 
         mWlo = mWhi;
     }
     dim3 grid((N + TN - 1) / TN, M / TM);
-    k_gemm_tc<P><<<grid, kThreads, Cfg<P>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, C, err);
+    k_gemm_tc<P, EPI><<<grid, kThreads, Cfg<P>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, e, err);
     BPM_CK(cudaGetLastError());
     return BPM_OK;
 }
@@ -329,10 +394,30 @@ int gemm_bf16x3_tc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi
         set_error("tensor-core GEMM needs M %% %d == 0, K %% %d == 0, N %% 16 == 0 (M=%d N=%d K=%d)", TM, TK, M, N, K);
         return BPM_ERR_ARG;
     }
-    if (products == 3) return launch<3>(s, M, N, K, Ahi, Alo, Whi, Wlo, C, err_flag);
-    if (products == 1) return launch<1>(s, M, N, K, Ahi, Alo, Whi, Wlo, C, err_flag);
+    TcEpilogue e{};
+    e.C = C;
+    e.ldc = N;
+    e.rows_valid = M;
+    e.cols_valid = N;
+    if (products == 3) return launch<3, TC_EPI_STORE>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
+    if (products == 1) return launch<1, TC_EPI_STORE>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
     set_error("products must be 1 or 3");
     return BPM_ERR_ARG;
+}
+
+int gemm_tc(cudaStream_t s, int epi, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* W,
+            const TcEpilogue& e, int* err_flag) {
+    if (M % TM || K % TK || N % 16 || M <= 0 || N <= 0) {
+        set_error("tensor-core GEMM needs M %% %d == 0, K %% %d == 0, N %% 16 == 0 (M=%d N=%d K=%d)", TM, TK, M, N, K);
+        return BPM_ERR_ARG;
+    }
+    switch (epi) {
+        case TC_EPI_STORE: return launch<1, TC_EPI_STORE>(s, M, N, K, A, A, W, W, e, err_flag);
+        case TC_EPI_BIAS_GELU: return launch<1, TC_EPI_BIAS_GELU>(s, M, N, K, A, A, W, W, e, err_flag);
+        case TC_EPI_BIAS_OUT: return launch<1, TC_EPI_BIAS_OUT>(s, M, N, K, A, A, W, W, e, err_flag);
+        case TC_EPI_GELU_BWD: return launch<1, TC_EPI_GELU_BWD>(s, M, N, K, A, A, W, W, e, err_flag);
+        default: set_error("unknown epilogue %d", epi); return BPM_ERR_ARG;
+    }
 }
 
 }  // namespace bpm

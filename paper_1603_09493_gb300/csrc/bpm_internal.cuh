@@ -68,6 +68,9 @@ struct HeadMap {
     float origin[3] = {0, 0, 0};
 };
 
+struct Mlp;
+void free_mlp(Mlp* m);
+
 }  // namespace bpm
 
 struct bpm_ctx {
@@ -77,6 +80,7 @@ struct bpm_ctx {
     bool own_stream = false;
     std::vector<bpm::Mesh*> meshes;
     std::vector<bpm::HeadMap*> maps;
+    std::vector<bpm::Mlp*> mlps;
 };
 
 namespace bpm {
@@ -86,6 +90,26 @@ int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets,
                   const int32_t* region, const bpm_region_mat* mats, int32_t n_regions,
                   uint32_t flags);
 void free_mesh(Mesh* M);
+
+// epilogues of the tensor-core GEMM (C = A W^T, BF16 operands, FP32 accumulate)
+enum { TC_EPI_STORE = 0, TC_EPI_BIAS_GELU = 1, TC_EPI_BIAS_OUT = 2, TC_EPI_GELU_BWD = 3 };
+struct TcEpilogue {
+    float* C = nullptr;            // FP32 [row][col] (STORE: result; BIAS_GELU: pre-activation z; BIAS_OUT: logits/probs)
+    int ldc = 0;
+    const float* bias = nullptr;   // [cols_valid]
+    __nv_bfloat16* H = nullptr;    // BF16 [row][col] (BIAS_GELU: activation; GELU_BWD: dz)
+    int ldh = 0;
+    __nv_bfloat16* HT = nullptr;   // BF16 [col][row], the transposed copy (optional)
+    int ldht = 0;
+    const float* Zin = nullptr;    // GELU_BWD: pre-activation [row][col]
+    int ldz = 0;
+    float* colsum = nullptr;       // GELU_BWD: per (32-row block, column) partial sums
+    int ldcs = 0;
+    int rows_valid = 0, cols_valid = 0;
+    int sigmoid = 0;               // BIAS_OUT: apply the logistic function
+};
+int gemm_tc(cudaStream_t s, int epi, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* W,
+            const TcEpilogue& e, int* err_flag);
 
 // demag GEMMs: C[M_rows][Nout] = A[M_rows][K] * W[Nout][K]^T, row strides lda/ldw/ldc (elements)
 int gemm_f32_nt(cudaStream_t s, int M_rows, int Nout, int K, const float* A, int lda,

@@ -8,12 +8,16 @@
 // m_{n+1} = N(m_n + h/2 (k1 + k2)), N(v) = v/|v|.
 //
 // Stage 1 (predictor) and stage 2 (corrector) each stage the island's source
-// state in shared memory for the exchange gather, evaluate the local field
-// terms, take the Heun stage, renormalise, and write the demag GEMM operand of
-// the new state (Ms * m, FP32 or BF16 hi/lo).  Stage 2 also updates the
-// volume-averaged <m_z> switch detector with a fixed-order block reduction.
-// The demag field B_d of the stage's source state comes from the GEMM that
-// ran just before the stage.
+// state in shared memory (component-planar, as in global memory) for the
+// exchange gather, evaluate the local field terms (the head map is read through
+// L1: staging the island's map window in shared memory was measured slower,
+// because the extra shared memory costs occupancy), take the Heun stage,
+// renormalise, and write the demag GEMM operand of the new state (Ms * m, FP32
+// or BF16 hi/lo).  Stage 2 also updates the volume-averaged
+// <m_z> switch detector with a fixed-order block reduction.  The demag field of
+// the stage's source state comes from the GEMM that ran just before the stage.
+#include <cmath>
+
 #include "bpm_step.cuh"
 
 namespace bpm {
@@ -32,41 +36,46 @@ __device__ __forceinline__ float3 normalize3(float3 v) {
     return r * v;
 }
 
+// continuous map coordinate of a point, clamped to the grid box
+__device__ __forceinline__ float map_coord(float p, float origin, float h, int n) {
+    float f = (p - origin) * (1.0f / h);
+    return fminf(fmaxf(f, 0.f), (float)(n - 1));
+}
+
+// trilinear interpolation of the head map (L1/L2-resident), clamped to the grid box
 __device__ __forceinline__ float3 trilinear(const StepArgs& a, float px, float py, float pz) {
-    float fx = (px - a.mox) / a.mh, fy = (py - a.moy) / a.mh, fz = (pz - a.moz) / a.mh;
-    fx = fminf(fmaxf(fx, 0.f), (float)(a.mx - 1));
-    fy = fminf(fmaxf(fy, 0.f), (float)(a.my - 1));
-    fz = fminf(fmaxf(fz, 0.f), (float)(a.mz - 1));
-    int ix = min((int)floorf(fx), a.mx - 2), iy = min((int)floorf(fy), a.my - 2),
-        iz = min((int)floorf(fz), a.mz - 2);
+    float fx = map_coord(px, a.mox, a.mh, a.mx), fy = map_coord(py, a.moy, a.mh, a.my),
+          fz = map_coord(pz, a.moz, a.mh, a.mz);
+    int ix = min((int)floorf(fx), a.mx - 2), iy = min((int)floorf(fy), a.my - 2), iz = min((int)floorf(fz), a.mz - 2);
     float wx = fx - ix, wy = fy - iy, wz = fz - iz;
     float3 acc = f3(0, 0, 0);
+    const float4* c0 = a.map + ((size_t)iz * a.my + iy) * a.mx + ix;
+    const int sy = a.mx, sz = a.mx * a.my;
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                float w = (dx ? wx : 1.f - wx) * (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
-                float4 v = __ldg(a.map + ((size_t)(iz + dz) * a.my + (iy + dy)) * a.mx + (ix + dx));
-                acc = acc + w * f3(v.x, v.y, v.z);
+                float ww = (dx ? wx : 1.f - wx) * (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
+                float4 v = __ldg(c0 + dz * sz + dy * sy + dx);
+                acc = acc + ww * f3(v.x, v.y, v.z);
             }
     return acc;
 }
 
-// effective field at node i of island b from the source state staged in smem
-__device__ __forceinline__ float3 eff_field(const StepArgs& a, int b, int i, float3 mi, const float* sm,
-                                            float4 p0, float4 p1, float4 p2, float ramp, float xh,
-                                            unsigned mask) {
+// effective field at node i of island b from the source state staged in smem ([3][n_pad])
+__device__ __forceinline__ float3 eff_field(const StepArgs& a, int b, int i, float3 mi, const float* sm, float4 p0,
+                                            float4 p1, float4 p2, float ramp, float xh, unsigned mask) {
     float3 B = f3(0, 0, 0);
     const int np = a.n_pad;
     if (mask & BPM_TERM_EXCHANGE) {
         int s = i >> 5, l = i & 31;
         int off = __ldg(a.sell_off + s);
-        int w = (__ldg(a.sell_off + s + 1) - off) >> 5;
+        int nw = (__ldg(a.sell_off + s + 1) - off) >> 5;
         const int2* ep = a.sell_ent + off + l;
         float bx = 0.f, by = 0.f, bz = 0.f;
-        for (int e = 0; e < w; ++e) {
+        for (int e = 0; e < nw; ++e) {
             int2 c = __ldg(ep + 32 * e);
             float v = __int_as_float(c.y);
             bx += v * (sm[c.x] - mi.x);
@@ -117,7 +126,8 @@ __device__ __forceinline__ void write_gemm_input(const StepArgs& a, int b, int i
     }
 }
 
-__device__ __forceinline__ void stage_to_smem(const float* src, float* sm, int n_pad) {
+// planar [3][n_pad] global state -> shared memory, 16-byte copies
+__device__ __forceinline__ void stage_state(const float* src, float* sm, int n_pad) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(sm);
     for (int q = threadIdx.x; q < 3 * n_pad / 4; q += blockDim.x) d4[q] = s4[q];
@@ -138,16 +148,17 @@ __device__ __forceinline__ double step_time(const StepArgs& a, int j) {
     return a.t0 + (double)(it * a.k + j) * a.h;
 }
 
-__global__ void __launch_bounds__(kStepThreads) k_stage1(StepArgs a, int j) {
-    extern __shared__ float sm[];
+__global__ void __launch_bounds__(kStepThreads, 6) k_stage1(StepArgs a, int j) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
     const int b = blockIdx.x;
     const int np = a.n_pad;
     const size_t base = (size_t)b * 3 * np;
-    stage_to_smem(a.m + base, sm, np);
     const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
     const double t = step_time(a, j);
     const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
     const float xh = a.x0 + a.v_nm_ps * (float)t;
+    stage_state(a.m + base, sm, np);
     const float hf = (float)a.h;
     __syncthreads();
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
@@ -165,17 +176,18 @@ __global__ void __launch_bounds__(kStepThreads) k_stage1(StepArgs a, int j) {
     }
 }
 
-__global__ void __launch_bounds__(kStepThreads) k_stage2(StepArgs a, int j) {
-    extern __shared__ float sm[];
+__global__ void __launch_bounds__(kStepThreads, 6) k_stage2(StepArgs a, int j) {
+    extern __shared__ float4 smem4[];
     __shared__ float red[kStepThreads / 32];
+    float* sm = reinterpret_cast<float*>(smem4);
     const int b = blockIdx.x;
     const int np = a.n_pad;
     const size_t base = (size_t)b * 3 * np;
-    stage_to_smem(a.ms + base, sm, np);
     const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
     const double t = step_time(a, j) + a.h;
     const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
     const float xh = a.x0 + a.v_nm_ps * (float)t;
+    stage_state(a.ms + base, sm, np);
     const float hh = 0.5f * (float)a.h;
     __syncthreads();
     float mzp = 0.f;
@@ -228,14 +240,15 @@ __global__ void __launch_bounds__(kStepThreads) k_init(StepArgs a) {
 }
 
 __global__ void __launch_bounds__(kStepThreads) k_field(StepArgs a, double t, unsigned mask, float* out) {
-    extern __shared__ float sm[];
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
     const int b = blockIdx.x;
     const int np = a.n_pad;
     const size_t base = (size_t)b * 3 * np;
-    stage_to_smem(a.m + base, sm, np);
     const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
     const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
     const float xh = a.x0 + a.v_nm_ps * (float)t;
+    stage_state(a.m + base, sm, np);
     __syncthreads();
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
@@ -248,27 +261,29 @@ __global__ void __launch_bounds__(kStepThreads) k_field(StepArgs a, double t, un
 
 __global__ void k_tick(long long* interval) { *interval += 1; }
 
+constexpr size_t kMaxStageSmem = 3 * sizeof(float) * kMaxNodes;
+
+size_t stage_smem_bytes(const StepArgs& a) { return 3 * sizeof(float) * (size_t)a.n_pad; }
+
 }  // namespace
 
 int configure_step_kernels() {
-    int smem = 3 * kMaxNodes * (int)sizeof(float);
+    int smem = (int)kMaxStageSmem;
     BPM_CK(cudaFuncSetAttribute(k_stage1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return BPM_OK;
 }
 
-static size_t smem_bytes(const StepArgs& a) { return 3 * (size_t)a.n_pad * sizeof(float); }
-
 void launch_stage1(const StepArgs& a, int j, cudaStream_t s) {
-    k_stage1<<<a.B, kStepThreads, smem_bytes(a), s>>>(a, j);
+    k_stage1<<<a.B, kStepThreads, stage_smem_bytes(a), s>>>(a, j);
 }
 void launch_stage2(const StepArgs& a, int j, cudaStream_t s) {
-    k_stage2<<<a.B, kStepThreads, smem_bytes(a), s>>>(a, j);
+    k_stage2<<<a.B, kStepThreads, stage_smem_bytes(a), s>>>(a, j);
 }
 void launch_init(const StepArgs& a, cudaStream_t s) { k_init<<<a.B, kStepThreads, 0, s>>>(a); }
 void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaStream_t s) {
-    k_field<<<a.B, kStepThreads, smem_bytes(a), s>>>(a, t, mask, out);
+    k_field<<<a.B, kStepThreads, stage_smem_bytes(a), s>>>(a, t, mask, out);
 }
 void launch_interval_tick(long long* interval, cudaStream_t s) { k_tick<<<1, 1, 0, s>>>(interval); }
 

@@ -364,3 +364,35 @@ def variant_island_mesh(diameter_nm: float, soft_ratio: float, elliptical: bool,
     _, K, hard, soft = best
     return layered_island_mesh(diameter_nm, t_hard, t_soft, rings=K, hard_slabs=hard,
                                soft_slabs=soft, aspect=1.5 if elliptical else 1.0, seed=seed)
+
+
+# --------------------------------------------------------------------------
+# surrogate inputs
+# --------------------------------------------------------------------------
+
+def mlp_init_params(sizes, seed: int) -> np.ndarray:
+    """Flat initial parameters of an MLP with layer widths `sizes` (input first):
+    per layer W [out][in] ~ N(0, 1/in) from the counter generator, then b = 0."""
+    out, k = [], 0
+    for i, (fan_in, fan_out) in enumerate(zip(sizes[:-1], sizes[1:])):
+        idx = np.arange(fan_in * fan_out, dtype=np.uint64)
+        W = counter_normal(seed, 1000 + i, idx) / math.sqrt(fan_in)
+        out.append(W.astype(np.float32))
+        out.append(np.zeros(fan_out, np.float32))
+    return np.concatenate(out)
+
+
+def unflatten_params(flat, sizes):
+    """Flat vector -> [(W [out][in], b [out]), ...] (float64), the oracle's layout."""
+    res, off = [], 0
+    for fan_in, fan_out in zip(sizes[:-1], sizes[1:]):
+        W = np.asarray(flat[off:off + fan_in * fan_out], np.float64).reshape(fan_out, fan_in)
+        off += fan_in * fan_out
+        b = np.asarray(flat[off:off + fan_out], np.float64)
+        off += fan_out
+        res.append((W, b))
+    return res
+
+
+def flatten_params(params) -> np.ndarray:
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float64)
