@@ -170,12 +170,18 @@ int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, i
 /* Batched LLG (Sec. II.C recording simulations, one batch of islands)     */
 /* ---------------------------------------------------------------------- */
 
-/* Create a batch of B islands that all use the same mesh (isl[b].mesh_id
- * equal for all b).  Device state is allocated here; the state starts at
- * m = +z, t = p->t0_ps.  Per step of size h = dt/substeps the batch runs the
- * Heun predictor and corrector (|m| renormalised after each), each preceded
- * by one demag GEMM over the whole batch, and updates the switch detector.
- * Errors: BPM_ERR_ARG (B < 1, mixed meshes, bad map id, substeps < 1). */
+/* Create a batch of B islands.  Islands may use different meshes (design
+ * variants of uneven size): they are grouped by mesh, each group with its own
+ * demag GEMM, and the groups of one output interval are captured into a
+ * single CUDA graph forked over up to four streams.  Device state is
+ * allocated here; the state starts at m = +z, t = p->t0_ps.  Per step of size
+ * h = dt/substeps every group runs the Heun predictor and corrector (|m|
+ * renormalised after each), each preceded by one demag GEMM over the group,
+ * and updates the switch detector.  Magnetisation arrays passed to the batch
+ * calls use a leading dimension ld >= the largest mesh's n_nodes; entries past
+ * an island's own n_nodes are not read and are left untouched (reads of host
+ * arrays leave them zero).
+ * Errors: BPM_ERR_ARG (B < 1, unknown mesh or map id, substeps < 1). */
 int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B,
                      const bpm_run_params* p, bpm_batch** out);
 /* Set the state: m (layout above, leading dimension ld) or NULL for +z, the

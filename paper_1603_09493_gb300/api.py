@@ -114,7 +114,7 @@ class Context:
     def run_batch(self, islands, params, n_intervals, precision=L.PREC_BF16X3, map_id=-1):
         isl = island_array(islands)
         q = run_params(params, precision, map_id)
-        n = self.mesh_info(int(isl["mesh_id"][0]))["n_nodes"]
+        n = max(self.mesh_info(int(mid))["n_nodes"] for mid in np.unique(isl["mesh_id"]))
         B = len(isl)
         m = np.zeros((B, 3, n), np.float32)
         sw = np.zeros(B, np.uint8)
@@ -207,7 +207,7 @@ class Batch:
         self.lib = ctx.lib
         self.isl = island_array(islands)
         self.B = len(self.isl)
-        self.n = ctx.mesh_info(int(self.isl["mesh_id"][0]))["n_nodes"]
+        self.n = max(ctx.mesh_info(int(mid))["n_nodes"] for mid in np.unique(self.isl["mesh_id"]))
         self.q = run_params(params, precision, map_id)
         h = c_void_p()
         L.check(self.lib.bpm_batch_create(ctx.h, L.ptr(self.isl), self.B, byref(self.q), byref(h)))

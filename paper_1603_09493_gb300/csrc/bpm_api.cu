@@ -23,23 +23,34 @@ static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 using namespace bpm;
 
-struct bpm_batch {
-    bpm_ctx* ctx = nullptr;
+// One mesh's share of a batch: its islands, state and demag buffers.
+struct Group {
     Mesh* mesh = nullptr;
-    HeadMap* map = nullptr;
     int B = 0, Bp = 0;
-    bpm_run_params p{};
+    std::vector<int> user_idx;    // batch island index of each group row
+    int* d_idx = nullptr;
     float4* isl = nullptr;
     float *m = nullptr, *ms = nullptr, *k1 = nullptr, *Hd = nullptr, *A32 = nullptr;
     __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr;
     float *mz_prev = nullptr, *t_sw = nullptr;
-    int *crossed = nullptr, *status = nullptr, *gemm_err = nullptr;
+    int *crossed = nullptr, *status = nullptr;
+    StepArgs args{};
+};
+
+struct bpm_batch {
+    bpm_ctx* ctx = nullptr;
+    HeadMap* map = nullptr;
+    int B = 0, n_max = 0;
+    bpm_run_params p{};
+    std::vector<Group> groups;
+    int* gemm_err = nullptr;
     long long* interval = nullptr;
     long long intervals_done = 0;
     double t0 = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    StepArgs args{};
+    std::vector<cudaStream_t> side;   // fork streams for the groups of a multi-mesh batch
+    std::vector<cudaEvent_t> ev;
 };
 
 namespace {
@@ -65,46 +76,70 @@ Mesh* get_mesh(bpm_ctx* ctx, int id) {
     return ctx->meshes[id];
 }
 
-// demag GEMM of the batch's current operand A -> Hd
-int run_demag_gemm(bpm_batch* bt, cudaStream_t s) {
-    Mesh* M = bt->mesh;
+// demag GEMM of a group's current operand A -> Hd
+int run_demag_gemm(bpm_batch* bt, Group& g, cudaStream_t s) {
+    Mesh* M = g.mesh;
     const int K = M->K();
     switch (bt->p.precision) {
         case BPM_PREC_FP32:
-            return gemm_f32_nt(s, bt->Bp, K, K, bt->A32, K, M->N32, K, bt->Hd, K);
+            return gemm_f32_nt(s, g.Bp, K, K, g.A32, K, M->N32, K, g.Hd, K);
         case BPM_PREC_BF16X3_REF:
-            return gemm_bf16x3_simt(s, bt->Bp, K, K, bt->Ahi, bt->Alo, M->Nhi, M->Nlo, bt->Hd, 3);
+            return gemm_bf16x3_simt(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 3);
         case BPM_PREC_BF16X3:
-            return gemm_bf16x3_tc(s, bt->Bp, K, K, bt->Ahi, bt->Alo, M->Nhi, M->Nlo, bt->Hd, 3, bt->gemm_err,
-                                  bt->ctx->sm_count);
+            return gemm_bf16x3_tc(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 3, bt->gemm_err, bt->ctx->sm_count);
         case BPM_PREC_BF16:
-            return gemm_bf16x3_tc(s, bt->Bp, K, K, bt->Ahi, bt->Alo, M->Nhi, M->Nlo, bt->Hd, 1, bt->gemm_err,
-                                  bt->ctx->sm_count);
+            return gemm_bf16x3_tc(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 1, bt->gemm_err, bt->ctx->sm_count);
         default:
             set_error("unknown precision %d", bt->p.precision);
             return BPM_ERR_ARG;
     }
 }
 
-int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
+int enqueue_group_interval(bpm_batch* bt, Group& g, cudaStream_t s) {
     for (int j = 0; j < bt->p.substeps; ++j) {
-        BPM_TRY(run_demag_gemm(bt, s));
-        launch_stage1(bt->args, j, s);
-        BPM_TRY(run_demag_gemm(bt, s));
-        launch_stage2(bt->args, j, s);
+        BPM_TRY(run_demag_gemm(bt, g, s));
+        launch_stage1(g.args, j, s);
+        BPM_TRY(run_demag_gemm(bt, g, s));
+        launch_stage2(g.args, j, s);
+    }
+    return BPM_OK;
+}
+
+// one output interval of every group; groups of a multi-mesh batch are forked
+// over side streams so that their kernels can run concurrently
+int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
+    if (bt->groups.size() == 1) {
+        BPM_TRY(enqueue_group_interval(bt, bt->groups[0], s));
+    } else {
+        const int ns = (int)bt->side.size();
+        BPM_CK(cudaEventRecord(bt->ev[0], s));
+        for (int k = 0; k < ns; ++k) BPM_CK(cudaStreamWaitEvent(bt->side[k], bt->ev[0], 0));
+        for (size_t gi = 0; gi < bt->groups.size(); ++gi)
+            BPM_TRY(enqueue_group_interval(bt, bt->groups[gi], bt->side[gi % ns]));
+        for (int k = 0; k < ns; ++k) {
+            BPM_CK(cudaEventRecord(bt->ev[1 + k], bt->side[k]));
+            BPM_CK(cudaStreamWaitEvent(s, bt->ev[1 + k], 0));
+        }
     }
     launch_interval_tick(bt->interval, s);
     BPM_CK(cudaGetLastError());
     return BPM_OK;
 }
 
+void free_group(Group& g) {
+    void* ptrs[] = {g.d_idx, g.isl, g.m, g.ms, g.k1, g.Hd, g.A32, g.Ahi, g.Alo, g.mz_prev, g.t_sw, g.crossed, g.status};
+    for (void* p : ptrs) cudaFree(p);
+}
+
 void free_batch(bpm_batch* bt) {
     if (!bt) return;
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     if (bt->graph) cudaGraphDestroy(bt->graph);
-    void* ptrs[] = {bt->isl, bt->m, bt->ms, bt->k1, bt->Hd, bt->A32, bt->Ahi, bt->Alo, bt->mz_prev,
-                    bt->t_sw, bt->crossed, bt->status, bt->gemm_err, bt->interval};
-    for (void* p : ptrs) cudaFree(p);
+    for (auto& g : bt->groups) free_group(g);
+    cudaFree(bt->gemm_err);
+    cudaFree(bt->interval);
+    for (auto s : bt->side) cudaStreamDestroy(s);
+    for (auto e : bt->ev) cudaEventDestroy(e);
     delete bt;
 }
 
@@ -309,13 +344,6 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         return BPM_ERR_ARG;
     }
     *out = nullptr;
-    Mesh* M = get_mesh(ctx, isl[0].mesh_id);
-    if (!M) return BPM_ERR_ARG;
-    for (int b = 1; b < B; ++b)
-        if (isl[b].mesh_id != isl[0].mesh_id) {
-            set_error("all islands of a batch must share one mesh (island %d)", b);
-            return BPM_ERR_ARG;
-        }
     if (p->substeps < 1 || !(p->dt_ps > 0) || p->precision < 0 || p->precision > 3) {
         set_error("bad run parameters (substeps >= 1, dt > 0, precision 0..3)");
         return BPM_ERR_ARG;
@@ -328,100 +356,134 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         }
         H = ctx->maps[p->map_id];
     }
+    // group the islands by mesh, in order of first appearance
+    std::vector<int> mesh_of_group;
+    std::vector<std::vector<int>> members;
+    for (int b = 0; b < B; ++b) {
+        const bpm_island& I = isl[b];
+        if (!get_mesh(ctx, I.mesh_id)) return BPM_ERR_ARG;
+        if (!(I.Ms_scale > 0) || !(I.Ku_scale >= 0)) {
+            set_error("island %d: Ms_scale must be > 0 and Ku_scale >= 0", b);
+            return BPM_ERR_ARG;
+        }
+        size_t gi = 0;
+        while (gi < mesh_of_group.size() && mesh_of_group[gi] != I.mesh_id) ++gi;
+        if (gi == mesh_of_group.size()) {
+            mesh_of_group.push_back(I.mesh_id);
+            members.emplace_back();
+        }
+        members[gi].push_back(b);
+    }
     BPM_TRY(ensure_device(ctx));
     bpm_batch* bt = new bpm_batch();
     bt->ctx = ctx;
-    bt->mesh = M;
     bt->map = H;
     bt->B = B;
-    bt->Bp = round_up(B, kIslandPad);
     bt->p = *p;
     bt->t0 = p->t0_ps;
-    const size_t K = (size_t)M->K();
-    const size_t S = (size_t)bt->Bp * K;
     int r = BPM_OK;
     auto chk = [&](int rr) {
         if (r == BPM_OK) r = rr;
     };
-    chk(dalloc(&bt->isl, 3 * (size_t)B));
-    chk(dalloc(&bt->m, S));
-    chk(dalloc(&bt->ms, S));
-    chk(dalloc(&bt->k1, S));
-    chk(dalloc(&bt->Hd, S));
-    if (p->precision == BPM_PREC_FP32)
-        chk(dalloc(&bt->A32, S));
-    else {
-        chk(dalloc(&bt->Ahi, S));
-        chk(dalloc(&bt->Alo, S));
-    }
-    chk(dalloc(&bt->mz_prev, B));
-    chk(dalloc(&bt->t_sw, B));
-    chk(dalloc(&bt->crossed, B));
-    chk(dalloc(&bt->status, B));
     chk(dalloc(&bt->gemm_err, 4));
     chk(dalloc(&bt->interval, 1));
+    bt->groups.resize(mesh_of_group.size());
+    for (size_t gi = 0; gi < bt->groups.size() && r == BPM_OK; ++gi) {
+        Group& g = bt->groups[gi];
+        Mesh* M = ctx->meshes[mesh_of_group[gi]];
+        g.mesh = M;
+        g.user_idx = members[gi];
+        g.B = (int)g.user_idx.size();
+        g.Bp = round_up(g.B, kIslandPad);
+        bt->n_max = std::max(bt->n_max, M->n);
+        const size_t S = (size_t)g.Bp * M->K();
+        chk(dalloc(&g.d_idx, g.B));
+        chk(dalloc(&g.isl, 3 * (size_t)g.B));
+        chk(dalloc(&g.m, S));
+        chk(dalloc(&g.ms, S));
+        chk(dalloc(&g.k1, S));
+        chk(dalloc(&g.Hd, S));
+        if (p->precision == BPM_PREC_FP32) {
+            chk(dalloc(&g.A32, S));
+        } else {
+            chk(dalloc(&g.Ahi, S));
+            chk(dalloc(&g.Alo, S));
+        }
+        chk(dalloc(&g.mz_prev, g.B));
+        chk(dalloc(&g.t_sw, g.B));
+        chk(dalloc(&g.crossed, g.B));
+        chk(dalloc(&g.status, g.B));
+        if (r != BPM_OK) break;
+        std::vector<float4> ip(3 * (size_t)g.B);
+        for (int k = 0; k < g.B; ++k) {
+            const bpm_island& I = isl[g.user_idx[k]];
+            ip[3 * k] = make_float4(1.f / I.Ms_scale, I.Ku_scale / I.Ms_scale, I.Ms_scale, 0.f);
+            ip[3 * k + 1] = make_float4(I.u[0], I.u[1], I.u[2], I.pos_nm[0]);
+            ip[3 * k + 2] = make_float4(I.pos_nm[1], I.Hext_T[0], I.Hext_T[1], I.Hext_T[2]);
+        }
+        cudaError_t e = cudaMemcpy(g.isl, ip.data(), ip.size() * sizeof(float4), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g.d_idx, g.user_idx.data(), g.B * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            set_error("island upload: %s", cudaGetErrorString(e));
+            r = BPM_ERR_CUDA;
+            break;
+        }
+        StepArgs& a = g.args;
+        a.B = g.B;
+        a.n = M->n;
+        a.n_pad = M->n_pad;
+        a.node_pos = M->node_pos;
+        a.node_mat = M->node_mat;
+        a.sell_off = M->sell_off;
+        a.sell_ent = M->sell_ent;
+        a.isl = g.isl;
+        a.map = H ? H->B : nullptr;
+        a.mx = H ? H->nx : 2;
+        a.my = H ? H->ny : 2;
+        a.mz = H ? H->nz : 2;
+        a.mh = H ? H->h : 1.f;
+        a.mox = H ? H->origin[0] : 0.f;
+        a.moy = H ? H->origin[1] : 0.f;
+        a.moz = H ? H->origin[2] : 0.f;
+        a.m = g.m;
+        a.ms = g.ms;
+        a.k1 = g.k1;
+        a.Hd = g.Hd;
+        a.A32 = g.A32;
+        a.Ahi = g.Ahi;
+        a.Alo = g.Alo;
+        a.prec = p->precision;
+        a.mz_prev = g.mz_prev;
+        a.t_sw = g.t_sw;
+        a.crossed = g.crossed;
+        a.status = g.status;
+        a.interval = bt->interval;
+        a.t0 = p->t0_ps;
+        a.k = p->substeps;
+        a.h = p->dt_ps / p->substeps;
+        a.alpha = (float)p->alpha;
+        a.gp = (float)(kGammaPs / (1.0 + p->alpha * p->alpha));
+        a.rise = (float)p->rise_ps;
+        a.v_nm_ps = (float)(p->v_m_per_s * 1e-3);
+        a.x0 = (float)p->x0_nm;
+        for (int c = 0; c < 3; ++c) a.uni[c] = p->uniform_T[c];
+        a.mask = p->term_mask;
+    }
+    if (r == BPM_OK && bt->groups.size() > 1) {
+        const int ns = (int)std::min<size_t>(4, bt->groups.size());
+        bt->side.resize(ns, nullptr);
+        bt->ev.resize(ns + 1, nullptr);
+        for (auto& st : bt->side)
+            if (r == BPM_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) r = BPM_ERR_CUDA;
+        for (auto& e : bt->ev)
+            if (r == BPM_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) r = BPM_ERR_CUDA;
+        if (r != BPM_OK) set_error("stream/event creation failed");
+    }
     if (r != BPM_OK) {
         free_batch(bt);
         return r;
     }
-    std::vector<float4> ip(3 * (size_t)B);
-    for (int b = 0; b < B; ++b) {
-        const bpm_island& I = isl[b];
-        if (!(I.Ms_scale > 0) || !(I.Ku_scale >= 0)) {
-            free_batch(bt);
-            set_error("island %d: Ms_scale must be > 0 and Ku_scale >= 0", b);
-            return BPM_ERR_ARG;
-        }
-        ip[3 * b] = make_float4(1.f / I.Ms_scale, I.Ku_scale / I.Ms_scale, I.Ms_scale, 0.f);
-        ip[3 * b + 1] = make_float4(I.u[0], I.u[1], I.u[2], I.pos_nm[0]);
-        ip[3 * b + 2] = make_float4(I.pos_nm[1], I.Hext_T[0], I.Hext_T[1], I.Hext_T[2]);
-    }
-    cudaError_t e = cudaMemcpy(bt->isl, ip.data(), ip.size() * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        free_batch(bt);
-        set_error("island upload: %s", cudaGetErrorString(e));
-        return BPM_ERR_CUDA;
-    }
-    StepArgs& a = bt->args;
-    a.B = B;
-    a.n = M->n;
-    a.n_pad = M->n_pad;
-    a.node_pos = M->node_pos;
-    a.node_mat = M->node_mat;
-    a.sell_off = M->sell_off;
-    a.sell_ent = M->sell_ent;
-    a.isl = bt->isl;
-    a.map = H ? H->B : nullptr;
-    a.mx = H ? H->nx : 2;
-    a.my = H ? H->ny : 2;
-    a.mz = H ? H->nz : 2;
-    a.mh = H ? H->h : 1.f;
-    a.mox = H ? H->origin[0] : 0.f;
-    a.moy = H ? H->origin[1] : 0.f;
-    a.moz = H ? H->origin[2] : 0.f;
-    a.m = bt->m;
-    a.ms = bt->ms;
-    a.k1 = bt->k1;
-    a.Hd = bt->Hd;
-    a.A32 = bt->A32;
-    a.Ahi = bt->Ahi;
-    a.Alo = bt->Alo;
-    a.prec = p->precision;
-    a.mz_prev = bt->mz_prev;
-    a.t_sw = bt->t_sw;
-    a.crossed = bt->crossed;
-    a.status = bt->status;
-    a.interval = bt->interval;
-    a.t0 = p->t0_ps;
-    a.k = p->substeps;
-    a.h = p->dt_ps / p->substeps;
-    a.alpha = (float)p->alpha;
-    a.gp = (float)(kGammaPs / (1.0 + p->alpha * p->alpha));
-    a.rise = (float)p->rise_ps;
-    a.v_nm_ps = (float)(p->v_m_per_s * 1e-3);
-    a.x0 = (float)p->x0_nm;
-    for (int c = 0; c < 3; ++c) a.uni[c] = p->uniform_T[c];
-    a.mask = p->term_mask;
     live_batches(ctx).push_back(bt);
     r = bpm_batch_set_state(bt, nullptr, 0, p->t0_ps, 0);
     if (r != BPM_OK) {
@@ -433,7 +495,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
 }
 
 namespace {
-__global__ void k_fill_plus_z(int B, int n, int n_pad, float* m) {
+__global__ void k_fill_plus_z(int n, int n_pad, float* m) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int b = blockIdx.y;
     if (i >= n) return;
@@ -442,14 +504,30 @@ __global__ void k_fill_plus_z(int B, int n, int n_pad, float* m) {
     m[base + n_pad + i] = 0.f;
     m[base + 2 * n_pad + i] = 1.f;
 }
-__global__ void k_read_flags(int B, const float* mz_prev, const float* t_sw, const int* status,
-                             uint8_t* switched, float* tsw_out, int* status_out, float* mz_out) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    if (switched) switched[b] = mz_prev[b] <= 0.f ? 1 : 0;
-    if (tsw_out) tsw_out[b] = t_sw[b];
-    if (status_out) status_out[b] = status[b];
-    if (mz_out) mz_out[b] = mz_prev[b];
+// user layout [B][3][ld] <-> group layout [Bg][3][n_pad], rows mapped through idx
+__global__ void k_gather_state(int n, int n_pad, int ld, const int* __restrict__ idx, const float* __restrict__ user,
+                               float* __restrict__ m) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y, b = row / 3, c = row % 3;
+    if (i >= n) return;
+    m[(size_t)row * n_pad + i] = user[((size_t)idx[b] * 3 + c) * ld + i];
+}
+__global__ void k_scatter_state(int n, int n_pad, int ld, const int* __restrict__ idx, const float* __restrict__ m,
+                                float* __restrict__ user) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int row = blockIdx.y, b = row / 3, c = row % 3;
+    if (i >= n) return;
+    user[((size_t)idx[b] * 3 + c) * ld + i] = m[(size_t)row * n_pad + i];
+}
+__global__ void k_scatter_flags(int Bg, const int* __restrict__ idx, const float* mz_prev, const float* t_sw,
+                                const int* status, uint8_t* switched, float* tsw_out, int* status_out, float* mz_out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Bg) return;
+    int b = idx[k];
+    if (switched) switched[b] = mz_prev[k] <= 0.f ? 1 : 0;
+    if (tsw_out) tsw_out[b] = t_sw[k];
+    if (status_out) status_out[b] = status[k];
+    if (mz_out) mz_out[b] = mz_prev[k];
 }
 }  // namespace
 
@@ -460,22 +538,27 @@ int bpm_batch_set_state(bpm_batch* bt, const float* m, int32_t ld, double t0_ps,
     }
     BPM_TRY(ensure_device(bt->ctx));
     cudaStream_t s = bt->ctx->stream;
-    const int n = bt->mesh->n, np = bt->mesh->n_pad;
-    if (m) {
-        if (ld < n) {
-            set_error("ld %d < n_nodes %d", ld, n);
-            return BPM_ERR_ARG;
-        }
-        BPM_CK(cudaMemcpy2DAsync(bt->m, np * sizeof(float), m, ld * sizeof(float), n * sizeof(float),
-                                 3 * (size_t)bt->B, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                 s));
-    } else {
-        k_fill_plus_z<<<dim3((n + 255) / 256, bt->B), 256, 0, s>>>(bt->B, n, np, bt->m);
+    if (m && ld < bt->n_max) {
+        set_error("ld %d < largest n_nodes %d", ld, bt->n_max);
+        return BPM_ERR_ARG;
     }
+    float* src = const_cast<float*>(m);
+    if (m && !on_device) {
+        BPM_CK(cudaMallocAsync(&src, sizeof(float) * 3 * (size_t)bt->B * ld, s));
+        BPM_CK(cudaMemcpyAsync(src, m, sizeof(float) * 3 * (size_t)bt->B * ld, cudaMemcpyHostToDevice, s));
+    }
+    for (auto& g : bt->groups) {
+        const int n = g.mesh->n, np = g.mesh->n_pad;
+        if (m)
+            k_gather_state<<<dim3((n + 255) / 256, 3 * g.B), 256, 0, s>>>(n, np, ld, g.d_idx, src, g.m);
+        else
+            k_fill_plus_z<<<dim3((n + 255) / 256, g.B), 256, 0, s>>>(n, np, g.m);
+    }
+    if (m && !on_device) cudaFreeAsync(src, s);
     BPM_CK(cudaMemsetAsync(bt->interval, 0, sizeof(long long), s));
     bt->t0 = t0_ps;
-    bt->args.t0 = t0_ps;
     bt->intervals_done = 0;
+    for (auto& g : bt->groups) g.args.t0 = t0_ps;
     // the interval graph bakes t0 into its kernel arguments: drop it
     if (bt->exec) {
         cudaGraphExecDestroy(bt->exec);
@@ -485,7 +568,7 @@ int bpm_batch_set_state(bpm_batch* bt, const float* m, int32_t ld, double t0_ps,
         cudaGraphDestroy(bt->graph);
         bt->graph = nullptr;
     }
-    launch_init(bt->args, s);
+    for (auto& g : bt->groups) launch_init(g.args, s);
     BPM_CK(cudaGetLastError());
     if (!on_device) BPM_CK(cudaStreamSynchronize(s));
     return BPM_OK;
@@ -519,80 +602,115 @@ int bpm_batch_advance(bpm_batch* bt, int32_t n_intervals) {
     return BPM_OK;
 }
 
-int bpm_batch_read(bpm_batch* bt, float* m, int32_t ld, uint8_t* switched, float* t_sw_ps, int32_t* status,
-                   float* mz, int on_device) {
+int bpm_batch_read(bpm_batch* bt, float* m, int32_t ld, uint8_t* switched, float* t_sw_ps, int32_t* status, float* mz,
+                   int on_device) {
     if (!bt) {
         set_error("null batch");
         return BPM_ERR_ARG;
     }
     BPM_TRY(ensure_device(bt->ctx));
     cudaStream_t s = bt->ctx->stream;
-    const int n = bt->mesh->n, np = bt->mesh->n_pad, B = bt->B;
-    if (m) {
-        if (ld < n) {
-            set_error("ld %d < n_nodes %d", ld, n);
-            return BPM_ERR_ARG;
+    const int B = bt->B;
+    if (m && ld < bt->n_max) {
+        set_error("ld %d < largest n_nodes %d", ld, bt->n_max);
+        return BPM_ERR_ARG;
+    }
+    // device staging of the outputs in the caller's island order
+    float *dm = on_device ? m : nullptr, *dtsw = on_device ? t_sw_ps : nullptr, *dmz = on_device ? mz : nullptr;
+    uint8_t* dsw = on_device ? switched : nullptr;
+    int* dst = on_device ? status : nullptr;
+    if (!on_device) {
+        if (m) {
+            BPM_CK(cudaMallocAsync(&dm, sizeof(float) * 3 * (size_t)B * ld, s));
+            BPM_CK(cudaMemsetAsync(dm, 0, sizeof(float) * 3 * (size_t)B * ld, s));
         }
-        BPM_CK(cudaMemcpy2DAsync(m, ld * sizeof(float), bt->m, np * sizeof(float), n * sizeof(float), 3 * (size_t)B,
-                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        BPM_CK(cudaMallocAsync(&dtsw, sizeof(float) * B, s));
+        BPM_CK(cudaMallocAsync(&dmz, sizeof(float) * B, s));
+        BPM_CK(cudaMallocAsync(&dsw, B, s));
+        BPM_CK(cudaMallocAsync(&dst, sizeof(int) * B, s));
     }
-    if (on_device) {
-        k_read_flags<<<(B + 255) / 256, 256, 0, s>>>(B, bt->mz_prev, bt->t_sw, bt->status, switched, t_sw_ps,
-                                                    status, mz);
-        BPM_CK(cudaGetLastError());
-        return BPM_OK;
+    for (auto& g : bt->groups) {
+        const int n = g.mesh->n, np = g.mesh->n_pad;
+        if (dm) k_scatter_state<<<dim3((n + 255) / 256, 3 * g.B), 256, 0, s>>>(n, np, ld, g.d_idx, g.m, dm);
+        k_scatter_flags<<<(g.B + 255) / 256, 256, 0, s>>>(g.B, g.d_idx, g.mz_prev, g.t_sw, g.status, dsw, dtsw, dst,
+                                                        dmz);
     }
-    std::vector<float> mzv(B), tsw(B);
-    std::vector<int> st(B);
+    BPM_CK(cudaGetLastError());
+    if (on_device) return BPM_OK;
     int gerr = 0;
     BPM_CK(cudaMemcpyAsync(&gerr, bt->gemm_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    BPM_CK(cudaMemcpyAsync(mzv.data(), bt->mz_prev, B * sizeof(float), cudaMemcpyDeviceToHost, s));
-    BPM_CK(cudaMemcpyAsync(tsw.data(), bt->t_sw, B * sizeof(float), cudaMemcpyDeviceToHost, s));
-    BPM_CK(cudaMemcpyAsync(st.data(), bt->status, B * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (m) BPM_CK(cudaMemcpyAsync(m, dm, sizeof(float) * 3 * (size_t)B * ld, cudaMemcpyDeviceToHost, s));
+    std::vector<float> tsw(B), mzv(B);
+    std::vector<int> stv(B);
+    std::vector<uint8_t> swv(B);
+    BPM_CK(cudaMemcpyAsync(tsw.data(), dtsw, sizeof(float) * B, cudaMemcpyDeviceToHost, s));
+    BPM_CK(cudaMemcpyAsync(mzv.data(), dmz, sizeof(float) * B, cudaMemcpyDeviceToHost, s));
+    BPM_CK(cudaMemcpyAsync(swv.data(), dsw, B, cudaMemcpyDeviceToHost, s));
+    BPM_CK(cudaMemcpyAsync(stv.data(), dst, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+    if (dm) cudaFreeAsync(dm, s);
+    cudaFreeAsync(dtsw, s);
+    cudaFreeAsync(dmz, s);
+    cudaFreeAsync(dsw, s);
+    cudaFreeAsync(dst, s);
     BPM_CK(cudaStreamSynchronize(s));
     if (gerr) {
         set_error("a bounded wait in the tensor-core demag GEMM gave up (code %d); results are invalid", gerr);
         return BPM_ERR_TIMEOUT;
     }
     for (int b = 0; b < B; ++b) {
-        if (switched) switched[b] = mzv[b] <= 0.f ? 1 : 0;
+        if (switched) switched[b] = swv[b];
         if (t_sw_ps) t_sw_ps[b] = tsw[b];
-        if (status) status[b] = st[b];
+        if (status) status[b] = stv[b];
         if (mz) mz[b] = mzv[b];
     }
     return BPM_OK;
 }
 
 int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out, int32_t ld, int on_device) {
-    if (!bt || !B_out || ld < (bt ? bt->mesh->n : 0)) {
+    if (!bt || !B_out || ld < bt->n_max) {
         set_error("bad field arguments");
         return BPM_ERR_ARG;
     }
     BPM_TRY(ensure_device(bt->ctx));
     cudaStream_t s = bt->ctx->stream;
-    const int n = bt->mesh->n, np = bt->mesh->n_pad;
-    float* out = nullptr;
-    BPM_CK(cudaMallocAsync(&out, (size_t)bt->Bp * 3 * np * sizeof(float), s));
+    const size_t user_bytes = sizeof(float) * 3 * (size_t)bt->B * ld;
+    float* dout = B_out;
+    if (!on_device) {
+        BPM_CK(cudaMallocAsync(&dout, user_bytes, s));
+        BPM_CK(cudaMemsetAsync(dout, 0, user_bytes, s));
+    }
     int r = BPM_OK;
-    if (term_mask & BPM_TERM_DEMAG) r = run_demag_gemm(bt, s);
-    if (r == BPM_OK) {
-        launch_field(bt->args, t_ps, term_mask, out, s);
-        cudaError_t e = cudaMemcpy2DAsync(B_out, ld * sizeof(float), out, np * sizeof(float), n * sizeof(float),
-                                          3 * (size_t)bt->B,
-                                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    for (auto& g : bt->groups) {
+        const int n = g.mesh->n, np = g.mesh->n_pad;
+        float* tmp = nullptr;
+        cudaError_t e = cudaMallocAsync(&tmp, (size_t)g.Bp * 3 * np * sizeof(float), s);
+        if (e != cudaSuccess) {
+            set_error("field scratch: %s", cudaGetErrorString(e));
+            r = BPM_ERR_OOM;
+            break;
+        }
+        if (term_mask & BPM_TERM_DEMAG) r = run_demag_gemm(bt, g, s);
+        if (r == BPM_OK) {
+            launch_field(g.args, t_ps, term_mask, tmp, s);
+            k_scatter_state<<<dim3((n + 255) / 256, 3 * g.B), 256, 0, s>>>(n, np, ld, g.d_idx, tmp, dout);
+        }
+        cudaFreeAsync(tmp, s);
+        if (r != BPM_OK) break;
+    }
+    if (r == BPM_OK && !on_device) {
+        cudaError_t e = cudaMemcpyAsync(B_out, dout, user_bytes, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) {
             set_error("field copy: %s", cudaGetErrorString(e));
             r = BPM_ERR_CUDA;
         }
     }
-    cudaFreeAsync(out, s);
+    if (!on_device) cudaFreeAsync(dout, s);
     if (r != BPM_OK) return r;
     if (!on_device) BPM_CK(cudaStreamSynchronize(s));
     return BPM_OK;
 }
 
-int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double* stage1_ms,
-                           double* stage2_ms) {
+int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double* stage1_ms, double* stage2_ms) {
     if (!bt || reps < 1) {
         set_error("bad kernel timing arguments");
         return BPM_ERR_ARG;
@@ -605,26 +723,28 @@ int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double*
     int r = BPM_OK;
     for (int q = 0; q < reps && r == BPM_OK; ++q) {
         int j = q % bt->p.substeps;
-        cudaEventRecord(ev[0], s);
-        r = run_demag_gemm(bt, s);
-        cudaEventRecord(ev[1], s);
-        launch_stage1(bt->args, j, s);
-        cudaEventRecord(ev[2], s);
-        if (r == BPM_OK) r = run_demag_gemm(bt, s);
-        cudaEventRecord(ev[3], s);
-        launch_stage2(bt->args, j, s);
-        cudaEventRecord(ev[4], s);
-        cudaError_t e = cudaEventSynchronize(ev[4]);
-        if (e != cudaSuccess) {
-            set_error("kernel timing: %s", cudaGetErrorString(e));
-            r = BPM_ERR_CUDA;
-            break;
+        for (auto& g : bt->groups) {
+            cudaEventRecord(ev[0], s);
+            r = run_demag_gemm(bt, g, s);
+            cudaEventRecord(ev[1], s);
+            launch_stage1(g.args, j, s);
+            cudaEventRecord(ev[2], s);
+            if (r == BPM_OK) r = run_demag_gemm(bt, g, s);
+            cudaEventRecord(ev[3], s);
+            launch_stage2(g.args, j, s);
+            cudaEventRecord(ev[4], s);
+            cudaError_t e = cudaEventSynchronize(ev[4]);
+            if (e != cudaSuccess) {
+                set_error("kernel timing: %s", cudaGetErrorString(e));
+                r = BPM_ERR_CUDA;
+                break;
+            }
+            float t[4];
+            for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
+            acc[0] += 0.5 * (t[0] + t[2]);
+            acc[1] += t[1];
+            acc[2] += t[3];
         }
-        float t[4];
-        for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
-        acc[0] += 0.5 * (t[0] + t[2]);
-        acc[1] += t[1];
-        acc[2] += t[3];
     }
     for (auto& e : ev) cudaEventDestroy(e);
     if (r != BPM_OK) return r;

@@ -396,3 +396,56 @@ def unflatten_params(flat, sizes):
 
 def flatten_params(params) -> np.ndarray:
     return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# uneven batches: design variants and track layouts
+# --------------------------------------------------------------------------
+
+def design_variants(n_min: int = 500, n_max: int = 4000, seed: int = 2):
+    """The 16 design variants of the uneven workload: diameter 6-10 nm (4
+    values) x soft/hard thickness ratio 0.2 or 0.5 x circular or 1.5:1
+    elliptical cross-section, with target node counts spread over
+    [n_min, n_max] in variant order."""
+    out = []
+    k = 0
+    for d in (6.0, 22.0 / 3.0, 26.0 / 3.0, 10.0):
+        for ratio in (0.2, 0.5):
+            for ell in (False, True):
+                target = int(round(n_min + (n_max - n_min) * k / 15.0))
+                mesh = variant_island_mesh(d, ratio, ell, target, seed=seed * 100 + k)
+                out.append(dict(mesh=mesh, diameter_nm=d, soft_ratio=ratio, elliptical=ell, target_nodes=target))
+                k += 1
+    return out
+
+
+def layout_offsets(layout: str, pitch_nm: float = 12.7):
+    """Positions (down-track x, cross-track y) of the target island and of the
+    adjacent-track islands under the fringing field: centered and shingled
+    writing have neighbours at (0, +-p); in staggered writing the adjacent
+    rows are shifted by half a pitch down-track, (+-p/2, +-p) (the effective
+    down-track separation is halved, Sec. IV).  Shingled writing keeps only
+    the previously written side.  Returns (target, [adjacent...])."""
+    p = float(pitch_nm)
+    if layout == "centered":
+        return (0.0, 0.0), [(0.0, p), (0.0, -p)]
+    if layout == "staggered":
+        return (0.0, 0.0), [(0.5 * p, p), (-0.5 * p, -p)]
+    if layout == "shingled":
+        return (0.0, 0.0), [(0.0, -p)]
+    raise ValueError(layout)
+
+
+def uneven_batch(variants, mesh_ids, realisations: int, seed: int, layout: str = "centered",
+                 pitch_nm: float = 12.7):
+    """Jittered targets plus adjacent-track islands for every variant; returns
+    (Islands, role) with role 0 = target, 1 = adjacent."""
+    parts, roles = [], []
+    (tx, ty), adj = layout_offsets(layout, pitch_nm)
+    for v, (var, mid) in enumerate(zip(variants, mesh_ids)):
+        for r, (px, py) in enumerate([(tx, ty)] + adj):
+            isl = jittered_islands(realisations, seed=seed, mesh_id=mid, lattice_pos_nm=(px, py),
+                                   first_index=(v * 8 + r) * realisations)
+            parts.append(isl)
+            roles.append(np.full(realisations, 0 if r == 0 else 1, np.int32))
+    return Islands.concat(parts), np.concatenate(roles)
