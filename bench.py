@@ -134,6 +134,53 @@ def stable_k(ctx, mid, hm, isl, p):
     return api.stable_substeps(api.field_bound(ctx, mid, isl, p, hm), p.dt_ps, p.alpha)
 
 
+def measure_plain(ctx, isl, p, hid, prec, n, islands=8, intervals=2):
+    """The one-island-per-launch FP32 GEMV form on a few islands of the same
+    workload, and the batched path on the same islands for the same-outcome check."""
+    sub = isl.subset(np.arange(islands))
+    plain = ctx.run_plain(sub, p, intervals, map_id=hid)
+    mixed = ctx.run_batch(sub, p, intervals, precision=prec, map_id=hid)
+    value = islands * intervals * DT_PS * 1e-3 / (plain["device_ms"] * 1e-3)
+    return {"value": value, "unit": UNIT, "islands": islands, "intervals": intervals,
+            "form": "one island per launch, FP32 GEMV demag streamed from HBM, single-island stage kernels",
+            "vs_mixed_max_abs_dm": float(np.abs(plain["m"] - mixed["m"]).max()),
+            "same_switch_flags": bool(np.array_equal(plain["switched"], mixed["switched"]))}
+
+
+def measure_surrogate(ctx, torch, stream, n_infer=16384, n_train=65536, batch=4096, reps=20):
+    """Surrogate MLP 16-256x4-2 (BF16 tensor-core GEMMs): inference evals/s on a
+    device-resident screening batch, training samples/s (AdamW steps)."""
+    from paper_1603_09493_gb300 import synth
+    sizes = [16, 256, 256, 256, 256, 2]
+    sur = ctx.surrogate((16, 256, 4, 2), synth.mlp_init_params(sizes, seed=3))
+    g = torch.Generator(device="cpu").manual_seed(0)
+    X = (torch.rand((n_infer, 16), generator=g) * 2 - 1).to("cuda")
+    Xt = (torch.rand((n_train, 16), generator=g) * 2 - 1).numpy()
+    Yt = (torch.rand((n_train, 2), generator=g) < 0.3).float().numpy()
+    for _ in range(3):
+        sur.infer(X)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        sur.infer(X)
+    e1.record(stream)
+    e1.synchronize()
+    infer_s = e0.elapsed_time(e1) * 1e-3 / reps
+    sur.train(Xt[:batch], Yt[:batch], epochs=1, batch=batch, lr=1e-3, weight_decay=1e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sur.train(Xt, Yt, epochs=1, batch=batch, lr=1e-3, weight_decay=1e-4)
+    train_s = time.perf_counter() - t0
+    flops_fwd = 2.0 * sum(a * b for a, b in zip(sizes[:-1], sizes[1:]))
+    sur.destroy()
+    return {"infer_evals_per_s": n_infer / infer_s, "infer_batch": n_infer,
+            "infer_tflops": flops_fwd * n_infer / infer_s / 1e12,
+            "train_samples_per_s": n_train / train_s, "train_batch": batch,
+            "note": "inference timed with CUDA events on device-resident inputs; training wall-clock per call "
+                    "including the host->device copy of the data"}
+
+
 def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -284,6 +331,10 @@ def main(args):
                "d2h_bytes_per_step": int(m_h.numel() * 4 + B * 9) / args.steps,
                "note": "one bpm_run_batch call per run of K intervals: batch setup, graph capture, island-table "
                        "H2D, K intervals, m_final/flags D2H"}
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["plain"] = measure_plain(ctx, isl, p, hid, prec, n)
+        extras["surrogate"] = measure_surrogate(ctx, torch, stream)
     ctx.close()
     if rank != 0:
         return 0
@@ -292,7 +343,7 @@ def main(args):
             "vs_baseline": None, "dtype": {"bf16x3": "bf16x3+f32", "fp32": "f32", "bf16": "bf16+f32"}[args.precision],
             "data": "synthetic", "config": config_dict(mesh, k, args.precision, B, world),
             "e2e": e2e, "gpu_launches": args.steps * (4 * k + 1), "roofline": roof, "roofline_step_kernels": roof_steps,
-            "kernel_ms": kt, "clocks": clocks, "status_ok": ok}
+            "kernel_ms": kt, "clocks": clocks, "status_ok": ok, **extras}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(mesh, mats, hm, p, k)
     print(json.dumps(line))
@@ -309,4 +360,5 @@ if __name__ == "__main__":
     ap.add_argument("--islands", type=int, default=B_ISLANDS)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     sys.exit(main(ap.parse_args()))

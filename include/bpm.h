@@ -219,6 +219,18 @@ int bpm_run_batch(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_
                   int32_t n_intervals, float* m_final, int32_t ld, uint8_t* switched,
                   float* t_sw_ps, int32_t* status);
 
+/* The plain form: every island integrated on its own, one island per launch,
+ * with an FP32 matrix-vector demag product streaming the operator from HBM in
+ * every Heun stage and single-island stage kernels (the per-island
+ * recording-simulation jobs of Sec. II.C ported to the GPU as is).  Same
+ * arithmetic per island as a BPM_PREC_FP32 batch; it exists as the baseline
+ * that the batched path is measured against.  Outputs are host arrays as in
+ * bpm_run_batch; device_ms (nullable) receives the summed CUDA-event time of
+ * the integration loops. */
+int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p,
+                  int32_t n_intervals, float* m_final, int32_t ld, uint8_t* switched, float* t_sw_ps,
+                  int32_t* status, double* device_ms);
+
 /* ---------------------------------------------------------------------- */
 /* Surrogate MLP (stands in for the Gaussian-process predictor of the      */
 /* efficient global optimisation, Sec. II.A)                               */

@@ -124,6 +124,21 @@ class Context:
                                        L.ptr(sw), L.ptr(tsw), L.ptr(st)))
         return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st)
 
+    def run_plain(self, islands, params, n_intervals, map_id=-1):
+        """One island per launch, FP32 GEMV demag (bpm_run_plain); returns results and device ms."""
+        isl = island_array(islands)
+        q = run_params(params, L.PREC_FP32, map_id)
+        n = max(self.mesh_info(int(mid))["n_nodes"] for mid in np.unique(isl["mesh_id"]))
+        B = len(isl)
+        m = np.zeros((B, 3, n), np.float32)
+        sw = np.zeros(B, np.uint8)
+        tsw = np.zeros(B, np.float32)
+        st = np.zeros(B, np.int32)
+        ms = c_double()
+        L.check(self.lib.bpm_run_plain(self.h, L.ptr(isl), B, byref(q), int(n_intervals), L.ptr(m), n, L.ptr(sw),
+                                       L.ptr(tsw), L.ptr(st), byref(ms)))
+        return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st, device_ms=ms.value)
+
     def llg_advance_noalloc(self, islands, params, n_intervals, m_dev, mz_dev=None, map_id=-1):
         """FP32 advance with no device allocation (bpm_llg_advance_noalloc):
         m_dev is a device tensor [B][3][ld] updated in place on the context stream."""

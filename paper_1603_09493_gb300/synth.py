@@ -449,3 +449,36 @@ def uneven_batch(variants, mesh_ids, realisations: int, seed: int, layout: str =
             parts.append(isl)
             roles.append(np.full(realisations, 0 if r == 0 else 1, np.int32))
     return Islands.concat(parts), np.concatenate(roles)
+
+
+# --------------------------------------------------------------------------
+# surrogate screening designs
+# --------------------------------------------------------------------------
+
+SCREEN_RANGES = dict(Ms_scale=(0.85, 1.15), Ku_scale=(0.75, 1.25), tilt_x_deg=(-4.0, 4.0),
+                     tilt_y_deg=(-4.0, 4.0), pos_x_nm=(-1.5, 1.5), pos_y_nm=(-1.5, 1.5),
+                     B_ext_T=(0.55, 1.05), angle_deg=(160.0, 180.0))
+
+
+def screening_designs(N: int, seed: int, mesh_id: int = 0, first_index: int = 0):
+    """Random candidate designs for the surrogate: per island uniform draws of
+    the parameters in SCREEN_RANGES (Ms and Ku scale, easy-axis tilt, position,
+    magnitude and angle from +z of a constant field in the xz-plane).  Returns
+    (Islands, X) with X [N][16] the features scaled to [-1, 1] (unused features
+    zero)."""
+    idx = np.arange(first_index, first_index + N, dtype=np.uint64)
+    keys = list(SCREEN_RANGES)
+    U = np.stack([counter_uniform(seed, 200 + k, idx) for k in range(len(keys))], 1)
+    val = {k: lo + (hi - lo) * U[:, j] for j, (k, (lo, hi)) in enumerate(SCREEN_RANGES.items())}
+    tx, ty = np.deg2rad(val["tilt_x_deg"]), np.deg2rad(val["tilt_y_deg"])
+    u = np.stack([np.tan(tx), np.tan(ty), np.ones(N)], 1)
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    a = np.deg2rad(val["angle_deg"])
+    H = np.stack([val["B_ext_T"] * np.sin(a), np.zeros(N), val["B_ext_T"] * np.cos(a)], 1)
+    isl = Islands(mesh_id=np.full(N, mesh_id, np.int32), Ms_scale=val["Ms_scale"].astype(np.float32),
+                  Ku_scale=val["Ku_scale"].astype(np.float32), u=u.astype(np.float32),
+                  pos_nm=np.stack([val["pos_x_nm"], val["pos_y_nm"]], 1).astype(np.float32),
+                  Hext_T=H.astype(np.float32))
+    X = np.zeros((N, 16), np.float32)
+    X[:, :len(keys)] = 2.0 * U - 1.0
+    return isl, X

@@ -190,3 +190,21 @@ def test_census_size_sampled_islands(ctx, headmap):
     ob = llg.Batch(ops, isl.subset(pick), p, head_map=hm)
     ref = ob.run()
     assert np.abs(out["m"][pick].transpose(0, 2, 1) - ref["m"]).max() <= 1e-3
+
+
+def test_plain_one_island_form_matches_batch_and_oracle(ctx, small, headmap):
+    # the one-island-per-launch baseline (FP32 GEMV demag) gives the same
+    # outcomes as the batched path; only the demag summation order differs
+    mesh, mats, ops, mid = small
+    hm, hid = headmap
+    isl = synth.jittered_islands(6, seed=61, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, t_end_ps=20.0, alpha=0.1, rise_ps=10.0, use_map=True, x0_nm=0.0,
+                        uniform_T=synth.uniform_field(0.6, 170.0))
+    p.substeps = llg.stable_substeps(llg.Batch(ops, isl, p, head_map=hm))
+    plain = ctx.run_plain(isl, p, p.n_intervals, map_id=hid)
+    batch = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_FP32, map_id=hid)
+    ref = llg.Batch(ops, isl, p, head_map=hm).run()
+    assert plain["device_ms"] > 0
+    assert np.abs(plain["m"] - batch["m"]).max() <= 1e-5
+    assert np.abs(plain["m"].transpose(0, 2, 1) - ref["m"]).max() <= 1e-3
+    assert np.array_equal(plain["switched"], batch["switched"])
