@@ -249,6 +249,11 @@ def main(args):
     k = stable_k(ctx, mid, hm, isl, p)
     p.substeps = k
     bt = ctx.batch(isl, p, precision=prec, map_id=hid)
+    tuning = None
+    if not args.no_autotune:
+        tuning = bt.autotune_cached(os.path.expanduser("~/.cache/bpmllg/tuning.json"),
+                                    torch.cuda.get_device_name(), reps=4)
+        bt.set_state(None, 0.0)
     for _ in range(max(args.warmup, 1)):
         bt.advance(1)
     stream.synchronize()
@@ -343,7 +348,7 @@ def main(args):
             "vs_baseline": None, "dtype": {"bf16x3": "bf16x3+f32", "fp32": "f32", "bf16": "bf16+f32"}[args.precision],
             "data": "synthetic", "config": config_dict(mesh, k, args.precision, B, world),
             "e2e": e2e, "gpu_launches": args.steps * (4 * k + 1), "roofline": roof, "roofline_step_kernels": roof_steps,
-            "kernel_ms": kt, "clocks": clocks, "status_ok": ok, **extras}
+            "kernel_ms": kt, "tuning": tuning, "clocks": clocks, "status_ok": ok, **extras}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(mesh, mats, hm, p, k)
     print(json.dumps(line))
@@ -361,4 +366,5 @@ if __name__ == "__main__":
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     sys.exit(main(ap.parse_args()))

@@ -209,6 +209,23 @@ int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out
  * clock does not; call bpm_batch_set_state afterwards to restart a run. */
 int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double* stage1_ms,
                            double* stage2_ms);
+/* Launch configuration of a batch's kernels. */
+typedef struct {
+    int32_t gemm_tile_n;     /* output columns per demag-GEMM CTA: 256 or 128 */
+    int32_t stage_threads;   /* threads per Heun-stage CTA: 128, 256 or 512 */
+    double  gemm_ms;         /* measured time of one demag GEMM over the batch (autotune output) */
+    double  stage_ms;        /* measured time of one predictor + one corrector over the batch */
+} bpm_tuning;
+
+/* Autotuner: time every (gemm_tile_n, stage_threads) candidate on this batch
+ * with CUDA events (reps Heun steps each, kernel by kernel), apply the fastest
+ * GEMM tile and stage CTA size, and report them in *chosen (nullable).  The
+ * state advances by the timed steps but the batch clock does not; call
+ * bpm_batch_set_state afterwards to restart a run.  Tile shapes are an
+ * implementation choice of this library, not of the paper. */
+int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen);
+/* Apply a tuning (for example one cached from an earlier autotune). */
+int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t);
 /* Current simulated time of the batch. */
 int bpm_batch_time(bpm_batch* bt, double* t_ps);
 int bpm_batch_destroy(bpm_batch* bt);

@@ -275,6 +275,40 @@ class Batch:
         L.check(self.lib.bpm_batch_kernel_times(self.h, int(reps), byref(g), byref(s1), byref(s2)))
         return dict(gemm_ms=g.value, stage1_ms=s1.value, stage2_ms=s2.value)
 
+    def autotune(self, reps: int = 4) -> dict:
+        t = L.bpm_tuning()
+        L.check(self.lib.bpm_batch_autotune(self.h, int(reps), byref(t)))
+        return dict(gemm_tile_n=t.gemm_tile_n, stage_threads=t.stage_threads, gemm_ms=t.gemm_ms,
+                    stage_ms=t.stage_ms)
+
+    def set_tuning(self, gemm_tile_n: int, stage_threads: int, **_):
+        t = L.bpm_tuning(int(gemm_tile_n), int(stage_threads), 0.0, 0.0)
+        L.check(self.lib.bpm_batch_set_tuning(self.h, byref(t)))
+
+    def tuning_key(self, device_name: str = "") -> str:
+        info = [self.ctx.mesh_info(int(mid))["n_pad"] for mid in np.unique(self.isl["mesh_id"])]
+        return f"{device_name}|npad={','.join(map(str, info))}|B={self.B}|prec={self.q.precision}"
+
+    def autotune_cached(self, cache_path: str, device_name: str = "", reps: int = 4) -> dict:
+        """Apply the tuning cached under this batch's key in a JSON file, or
+        autotune, store the choice and apply it."""
+        import json
+        import os
+        key = self.tuning_key(device_name)
+        cache = {}
+        if os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+        if key in cache:
+            self.set_tuning(**cache[key])
+            return dict(cache[key], cached=True)
+        t = self.autotune(reps)
+        cache[key] = t
+        os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        return dict(t, cached=False)
+
     def time(self) -> float:
         t = c_double()
         L.check(self.lib.bpm_batch_time(self.h, byref(t)))

@@ -51,6 +51,7 @@ struct bpm_batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaStream_t> side;   // fork streams for the groups of a multi-mesh batch
     std::vector<cudaEvent_t> ev;
+    int tile_n = 256;                 // demag GEMM output columns per CTA
 };
 
 namespace {
@@ -86,9 +87,9 @@ int run_demag_gemm(bpm_batch* bt, Group& g, cudaStream_t s) {
         case BPM_PREC_BF16X3_REF:
             return gemm_bf16x3_simt(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 3);
         case BPM_PREC_BF16X3:
-            return gemm_bf16x3_tc(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 3, bt->gemm_err, bt->ctx->sm_count);
+            return gemm_bf16x3_tc(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 3, bt->gemm_err, bt->tile_n);
         case BPM_PREC_BF16:
-            return gemm_bf16x3_tc(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 1, bt->gemm_err, bt->ctx->sm_count);
+            return gemm_bf16x3_tc(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 1, bt->gemm_err, bt->tile_n);
         default:
             set_error("unknown precision %d", bt->p.precision);
             return BPM_ERR_ARG;
@@ -129,6 +130,17 @@ int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
 void free_group(Group& g) {
     void* ptrs[] = {g.d_idx, g.isl, g.m, g.ms, g.k1, g.Hd, g.A32, g.Ahi, g.Alo, g.mz_prev, g.t_sw, g.crossed, g.status};
     for (void* p : ptrs) cudaFree(p);
+}
+
+void drop_graph(bpm_batch* bt) {
+    if (bt->exec) {
+        cudaGraphExecDestroy(bt->exec);
+        bt->exec = nullptr;
+    }
+    if (bt->graph) {
+        cudaGraphDestroy(bt->graph);
+        bt->graph = nullptr;
+    }
 }
 
 void free_batch(bpm_batch* bt) {
@@ -212,7 +224,11 @@ void bpm_destroy(bpm_ctx* ctx) {
     for (Mesh* m : ctx->meshes) free_mesh(m);
     for (Mlp* m : ctx->mlps) free_mlp(m);
     for (HeadMap* h : ctx->maps) {
-        if (h) cudaFree(h->B);
+        if (h) {
+            if (h->tex) cudaDestroyTextureObject(h->tex);
+            if (h->arr) cudaFreeArray(h->arr);
+            cudaFree(h->B);
+        }
         delete h;
     }
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -327,7 +343,30 @@ int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, i
     for (int a = 0; a < 3; ++a) H->origin[a] = origin_nm[a];
     cudaError_t e = cudaMalloc(&H->B, N * sizeof(float4));
     if (e == cudaSuccess) e = cudaMemcpy(H->B, v.data(), N * sizeof(float4), cudaMemcpyHostToDevice);
+    cudaChannelFormatDesc cd = cudaCreateChannelDesc<float4>();
+    cudaExtent ext = make_cudaExtent(nx, ny, nz);
+    if (e == cudaSuccess) e = cudaMalloc3DArray(&H->arr, &cd, ext);
+    if (e == cudaSuccess) {
+        cudaMemcpy3DParms cp = {};
+        cp.srcPtr = make_cudaPitchedPtr(v.data(), nx * sizeof(float4), nx, ny);
+        cp.dstArray = H->arr;
+        cp.extent = ext;
+        cp.kind = cudaMemcpyHostToDevice;
+        e = cudaMemcpy3D(&cp);
+    }
+    if (e == cudaSuccess) {
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = H->arr;
+        cudaTextureDesc td = {};
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&H->tex, &rd, &td, nullptr);
+    }
     if (e != cudaSuccess) {
+        if (H->arr) cudaFreeArray(H->arr);
         cudaFree(H->B);
         delete H;
         set_error("head map upload: %s", cudaGetErrorString(e));
@@ -439,6 +478,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         a.sell_ent = M->sell_ent;
         a.isl = g.isl;
         a.map = H ? H->B : nullptr;
+        a.tex = H ? H->tex : 0;
         a.mx = H ? H->nx : 2;
         a.my = H ? H->ny : 2;
         a.mz = H ? H->nz : 2;
@@ -469,6 +509,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         a.x0 = (float)p->x0_nm;
         for (int c = 0; c < 3; ++c) a.uni[c] = p->uniform_T[c];
         a.mask = p->term_mask;
+        a.threads = 256;
     }
     if (r == BPM_OK && bt->groups.size() > 1) {
         const int ns = (int)std::min<size_t>(4, bt->groups.size());
@@ -560,14 +601,7 @@ int bpm_batch_set_state(bpm_batch* bt, const float* m, int32_t ld, double t0_ps,
     bt->intervals_done = 0;
     for (auto& g : bt->groups) g.args.t0 = t0_ps;
     // the interval graph bakes t0 into its kernel arguments: drop it
-    if (bt->exec) {
-        cudaGraphExecDestroy(bt->exec);
-        bt->exec = nullptr;
-    }
-    if (bt->graph) {
-        cudaGraphDestroy(bt->graph);
-        bt->graph = nullptr;
-    }
+    drop_graph(bt);
     for (auto& g : bt->groups) launch_init(g.args, s);
     BPM_CK(cudaGetLastError());
     if (!on_device) BPM_CK(cudaStreamSynchronize(s));
@@ -751,6 +785,52 @@ int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double*
     if (gemm_ms) *gemm_ms = acc[0] / reps;
     if (stage1_ms) *stage1_ms = acc[1] / reps;
     if (stage2_ms) *stage2_ms = acc[2] / reps;
+    return BPM_OK;
+}
+
+int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
+    if (!bt || !t || (t->gemm_tile_n != 128 && t->gemm_tile_n != 256) ||
+        (t->stage_threads != 128 && t->stage_threads != 256 && t->stage_threads != 512)) {
+        set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512)");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    BPM_CK(cudaStreamSynchronize(bt->ctx->stream));
+    bt->tile_n = t->gemm_tile_n;
+    for (auto& g : bt->groups) g.args.threads = t->stage_threads;
+    drop_graph(bt);   // the graph holds the old launch configurations
+    return BPM_OK;
+}
+
+int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
+    if (!bt || reps < 1) {
+        set_error("bad autotune arguments");
+        return BPM_ERR_ARG;
+    }
+    const int tiles[2] = {256, 128};
+    const int threads[3] = {256, 128, 512};
+    const bool tc = bt->p.precision == BPM_PREC_BF16X3 || bt->p.precision == BPM_PREC_BF16;
+    double best_g = 1e300, best_s = 1e300;
+    int bt_n = 256, bt_t = 256;
+    for (int ti = 0; ti < (tc ? 2 : 1); ++ti)
+        for (int hi = 0; hi < 3; ++hi) {
+            bpm_tuning t{tiles[ti], threads[hi], 0, 0};
+            BPM_TRY(bpm_batch_set_tuning(bt, &t));
+            double g = 0, s1 = 0, s2 = 0;
+            BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));   // warm-up
+            BPM_TRY(bpm_batch_kernel_times(bt, reps, &g, &s1, &s2));
+            if (hi == 0 && g < best_g) {
+                best_g = g;
+                bt_n = tiles[ti];
+            }
+            if (ti == 0 && s1 + s2 < best_s) {
+                best_s = s1 + s2;
+                bt_t = threads[hi];
+            }
+        }
+    bpm_tuning t{bt_n, bt_t, best_g, best_s};
+    BPM_TRY(bpm_batch_set_tuning(bt, &t));
+    if (chosen) *chosen = t;
     return BPM_OK;
 }
 

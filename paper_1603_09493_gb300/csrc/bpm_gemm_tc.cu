@@ -22,8 +22,12 @@ namespace bpm {
 
 namespace {
 
-constexpr int TM = 128, TN = 256, TK = 64;                  // tile, TK = one 128 B swizzle row of BF16
-constexpr int A_TILE = TM * TK * 2, W_TILE = TN * TK * 2;    // 16 KB, 32 KB
+constexpr int TM = 128, TK = 64;           // output rows per CTA; TK = one 128 B swizzle row of BF16
+constexpr int A_TILE = TM * TK * 2;         // 16 KB
+template <int TN>
+struct Tile {
+    static constexpr int W_TILE = TN * TK * 2;   // 32 KB (TN = 256) or 16 KB (TN = 128)
+};
 constexpr unsigned long long kWaitNs = 200000000ull;      // 200 ms per wait (a normal wait is < 0.1 ms)
 constexpr int kThreads = 128;
 
@@ -93,13 +97,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
     return d;
 }
 
-// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128, N = 256
-constexpr uint32_t kIdesc = (1u << 4)              // D = F32
-                            | (1u << 7)            // A = BF16
-                            | (1u << 10)           // B = BF16
-                            | ((uint32_t)(TN >> 3) << 17)
-                            | ((uint32_t)(TM >> 4) << 24);
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128, N = TN
+template <int TN>
+struct Idesc {
+    static constexpr uint32_t value = (1u << 4)              // D = F32
+                                      | (1u << 7)            // A = BF16
+                                      | (1u << 10)           // B = BF16
+                                      | ((uint32_t)(TN >> 3) << 17)
+                                      | ((uint32_t)(TM >> 4) << 24);
+};
 
+template <int TN>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
     asm volatile(
         "{\n"
@@ -107,7 +115,7 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t
         "setp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
         "}\n" ::"r"(tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(Idesc<TN>::value), "r"(accumulate)
         : "memory");
 }
 
@@ -127,10 +135,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int P>
+template <int P, int TN>
 struct Cfg {
+    static constexpr int W_TILE = Tile<TN>::W_TILE;
     static constexpr int stage_bytes = (P == 3 ? 2 : 1) * (A_TILE + W_TILE);
-    static constexpr int stages = (P == 3) ? 2 : 4;
+    static constexpr int stages = (192 * 1024) / stage_bytes;   // 2 (P=3, TN=256) .. 6
     static constexpr int smem = stages * stage_bytes + 1024 /*align*/ + 256 /*barriers*/;
 };
 
@@ -195,12 +204,13 @@ __device__ __forceinline__ void epilogue32(const TcEpilogue& e, int M, int N, in
     }
 }
 
-template <int P, int EPI>
+template <int P, int EPI, int TN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
               const __grid_constant__ CUtensorMap mWhi, const __grid_constant__ CUtensorMap mWlo, int M, int N, int K,
               const TcEpilogue e, int* err) {
-    using CF = Cfg<P>;
+    using CF = Cfg<P, TN>;
+    constexpr int W_TILE = CF::W_TILE;
     constexpr int S = CF::stages;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -274,11 +284,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int k = 0; k < TK / 16; ++k) {
                 const uint32_t koff = 32u * k;
                 const uint64_t ahi = sw128_desc(sAhi(s) + koff), whi = sw128_desc(sWhi(s) + koff);
-                mma_bf16(tmem, ahi, whi, (kb > 0 || k > 0) ? 1u : 0u);
+                mma_bf16<TN>(tmem, ahi, whi, (kb > 0 || k > 0) ? 1u : 0u);
                 if (P == 3) {
                     const uint64_t alo = sw128_desc(sAlo(s) + koff), wlo = sw128_desc(sWlo(s) + koff);
-                    mma_bf16(tmem, alo, whi, 1u);
-                    mma_bf16(tmem, ahi, wlo, 1u);
+                    mma_bf16<TN>(tmem, alo, whi, 1u);
+                    mma_bf16<TN>(tmem, ahi, wlo, 1u);
                 }
             }
             mma_commit(empty_bar(s));
@@ -361,12 +371,13 @@ int make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_row
     return BPM_OK;
 }
 
-template <int P, int EPI>
+template <int P, int EPI, int TN = 256>
 int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
            const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, const TcEpilogue& e, int* err) {
     static bool configured = false;
     if (!configured) {
-        BPM_CK(cudaFuncSetAttribute(k_gemm_tc<P, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<P>::smem));
+        BPM_CK(cudaFuncSetAttribute(k_gemm_tc<P, EPI, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Cfg<P, TN>::smem));
         configured = true;
     }
     CUtensorMap mAhi, mAlo, mWhi, mWlo;
@@ -380,7 +391,7 @@ int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const 
         mWlo = mWhi;
     }
     dim3 grid((N + TN - 1) / TN, M / TM);
-    k_gemm_tc<P, EPI><<<grid, kThreads, Cfg<P>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, e, err);
+    k_gemm_tc<P, EPI, TN><<<grid, kThreads, Cfg<P, TN>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, e, err);
     BPM_CK(cudaGetLastError());
     return BPM_OK;
 }
@@ -389,7 +400,7 @@ int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const 
 
 int gemm_bf16x3_tc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
                    const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, float* C, int products, int* err_flag,
-                   int /*sm_count*/) {
+                   int tile_n) {
     if (M % TM || K % TK || N % 16 || M <= 0 || N <= 0) {
         set_error("tensor-core GEMM needs M %% %d == 0, K %% %d == 0, N %% 16 == 0 (M=%d N=%d K=%d)", TM, TK, M, N, K);
         return BPM_ERR_ARG;
@@ -399,8 +410,13 @@ int gemm_bf16x3_tc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi
     e.ldc = N;
     e.rows_valid = M;
     e.cols_valid = N;
-    if (products == 3) return launch<3, TC_EPI_STORE>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
-    if (products == 1) return launch<1, TC_EPI_STORE>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
+    if (tile_n == 128) {
+        if (products == 3) return launch<3, TC_EPI_STORE, 128>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
+        if (products == 1) return launch<1, TC_EPI_STORE, 128>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
+    } else {
+        if (products == 3) return launch<3, TC_EPI_STORE, 256>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
+        if (products == 1) return launch<1, TC_EPI_STORE, 256>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
+    }
     set_error("products must be 1 or 3");
     return BPM_ERR_ARG;
 }

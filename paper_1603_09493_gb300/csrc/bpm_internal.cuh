@@ -63,6 +63,8 @@ struct Mesh {
 
 struct HeadMap {
     float4* B = nullptr;          // [nz][ny][nx] (Bx, By, Bz, 0)
+    cudaArray_t arr = nullptr;    // the same voxels in a 3-D array, read through the texture path
+    cudaTextureObject_t tex = 0;  // point sampling, unnormalised coordinates, clamped
     int nx = 0, ny = 0, nz = 0;
     float h = 1.f;
     float origin[3] = {0, 0, 0};
@@ -119,6 +121,6 @@ int gemm_bf16x3_simt(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* A
                      float* C, int products);
 int gemm_bf16x3_tc(cudaStream_t s, int M_rows, int Nout, int K, const __nv_bfloat16* Ahi,
                    const __nv_bfloat16* Alo, const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo,
-                   float* C, int products, int* err_flag, int sm_count);
+                   float* C, int products, int* err_flag, int tile_n);
 
 }  // namespace bpm

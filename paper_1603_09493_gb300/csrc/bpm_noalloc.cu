@@ -158,6 +158,7 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
     a.sell_ent = M->sell_ent;
     a.isl = reinterpret_cast<const float4*>(s8 + o_isl);
     a.map = H ? H->B : nullptr;
+    a.tex = H ? H->tex : 0;
     a.mx = H ? H->nx : 2;
     a.my = H ? H->ny : 2;
     a.mz = H ? H->nz : 2;

@@ -109,6 +109,7 @@ extern "C" int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, con
         a.sell_ent = M->sell_ent;
         a.isl = d_isl;
         a.map = H ? H->B : nullptr;
+        a.tex = H ? H->tex : 0;
         a.mx = H ? H->nx : 2;
         a.my = H ? H->ny : 2;
         a.mz = H ? H->nz : 2;

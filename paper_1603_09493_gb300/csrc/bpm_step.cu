@@ -42,15 +42,15 @@ __device__ __forceinline__ float map_coord(float p, float origin, float h, int n
     return fminf(fmaxf(f, 0.f), (float)(n - 1));
 }
 
-// trilinear interpolation of the head map (L1/L2-resident), clamped to the grid box
+// trilinear interpolation of the head map, clamped to the grid box; voxels come
+// from the texture path with point sampling, so the arithmetic is the plain FP32
+// trilinear blend of the stored values
 __device__ __forceinline__ float3 trilinear(const StepArgs& a, float px, float py, float pz) {
     float fx = map_coord(px, a.mox, a.mh, a.mx), fy = map_coord(py, a.moy, a.mh, a.my),
           fz = map_coord(pz, a.moz, a.mh, a.mz);
     int ix = min((int)floorf(fx), a.mx - 2), iy = min((int)floorf(fy), a.my - 2), iz = min((int)floorf(fz), a.mz - 2);
     float wx = fx - ix, wy = fy - iy, wz = fz - iz;
     float3 acc = f3(0, 0, 0);
-    const float4* c0 = a.map + ((size_t)iz * a.my + iy) * a.mx + ix;
-    const int sy = a.mx, sz = a.mx * a.my;
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
@@ -58,7 +58,7 @@ __device__ __forceinline__ float3 trilinear(const StepArgs& a, float px, float p
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
                 float ww = (dx ? wx : 1.f - wx) * (dy ? wy : 1.f - wy) * (dz ? wz : 1.f - wz);
-                float4 v = __ldg(c0 + dz * sz + dy * sy + dx);
+                float4 v = tex3D<float4>(a.tex, ix + dx + 0.5f, iy + dy + 0.5f, iz + dz + 0.5f);
                 acc = acc + ww * f3(v.x, v.y, v.z);
             }
     return acc;
@@ -148,7 +148,9 @@ __device__ __forceinline__ double step_time(const StepArgs& a, int j) {
     return a.t0 + (double)(it * a.k + j) * a.h;
 }
 
-__global__ void __launch_bounds__(kStepThreads, 6) k_stage1(StepArgs a, int j) {
+// occupancy bound: 1536 resident threads per SM (at most 40 registers each)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1536 / NT) k_stage1(StepArgs a, int j) {
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
     const int b = blockIdx.x;
@@ -176,9 +178,10 @@ __global__ void __launch_bounds__(kStepThreads, 6) k_stage1(StepArgs a, int j) {
     }
 }
 
-__global__ void __launch_bounds__(kStepThreads, 6) k_stage2(StepArgs a, int j) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1536 / NT) k_stage2(StepArgs a, int j) {
     extern __shared__ float4 smem4[];
-    __shared__ float red[kStepThreads / 32];
+    __shared__ float red[NT / 32];
     float* sm = reinterpret_cast<float*>(smem4);
     const int b = blockIdx.x;
     const int np = a.n_pad;
@@ -269,17 +272,33 @@ size_t stage_smem_bytes(const StepArgs& a) { return 3 * sizeof(float) * (size_t)
 
 int configure_step_kernels() {
     int smem = (int)kMaxStageSmem;
-    BPM_CK(cudaFuncSetAttribute(k_stage1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    BPM_CK(cudaFuncSetAttribute(k_stage2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage1<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage1<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage1<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage2<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage2<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage2<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return BPM_OK;
 }
 
 void launch_stage1(const StepArgs& a, int j, cudaStream_t s) {
-    k_stage1<<<a.B, kStepThreads, stage_smem_bytes(a), s>>>(a, j);
+    const size_t sm = stage_smem_bytes(a);
+    if (a.threads == 128)
+        k_stage1<128><<<a.B, 128, sm, s>>>(a, j);
+    else if (a.threads == 512)
+        k_stage1<512><<<a.B, 512, sm, s>>>(a, j);
+    else
+        k_stage1<256><<<a.B, 256, sm, s>>>(a, j);
 }
 void launch_stage2(const StepArgs& a, int j, cudaStream_t s) {
-    k_stage2<<<a.B, kStepThreads, stage_smem_bytes(a), s>>>(a, j);
+    const size_t sm = stage_smem_bytes(a);
+    if (a.threads == 128)
+        k_stage2<128><<<a.B, 128, sm, s>>>(a, j);
+    else if (a.threads == 512)
+        k_stage2<512><<<a.B, 512, sm, s>>>(a, j);
+    else
+        k_stage2<256><<<a.B, 256, sm, s>>>(a, j);
 }
 void launch_init(const StepArgs& a, cudaStream_t s) { k_init<<<a.B, kStepThreads, 0, s>>>(a); }
 void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaStream_t s) {

@@ -11,7 +11,8 @@ struct StepArgs {
     const int* sell_off;
     const int2* sell_ent;
     const float4* isl;        // [B][3] (1/Ms_s, Ku_s/Ms_s, Ms_s, 0), (u, pos_x), (pos_y, Hext)
-    const float4* map;        // head map or nullptr
+    const float4* map;        // head map (linear copy) or nullptr: no head field
+    cudaTextureObject_t tex;  // head map voxels for the lookups
     int mx, my, mz;
     float mh, mox, moy, moz;
     float* m;                 // [Bp][3][n_pad]
@@ -33,6 +34,7 @@ struct StepArgs {
     float rise, v_nm_ps, x0;
     float uni[3];
     unsigned mask;
+    int threads;              // CTA size of the stage kernels: 128, 256 or 512 (autotuned)
 };
 
 constexpr int kStepThreads = 256;

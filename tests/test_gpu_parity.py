@@ -208,3 +208,29 @@ def test_plain_one_island_form_matches_batch_and_oracle(ctx, small, headmap):
     assert np.abs(plain["m"] - batch["m"]).max() <= 1e-5
     assert np.abs(plain["m"].transpose(0, 2, 1) - ref["m"]).max() <= 1e-3
     assert np.array_equal(plain["switched"], batch["switched"])
+
+
+def test_autotuner_choices_do_not_change_results(ctx, small, headmap):
+    # tile width and CTA size are launch shapes only: m is bitwise identical
+    # for every tuning; <m_z> sums in a CTA-size dependent order (last bits)
+    mesh, mats, ops, mid = small
+    hm, hid = headmap
+    isl = synth.jittered_islands(300, seed=71, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, substeps=8, alpha=0.1, rise_ps=10.0, use_map=True,
+                        uniform_T=synth.uniform_field(0.7, 170.0))
+    outs = []
+    for tn, nt in [(256, 256), (128, 128), (256, 512), (128, 256)]:
+        with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+            bt.set_tuning(tn, nt)
+            bt.advance(20)
+            outs.append(bt.read())
+    for o in outs[1:]:
+        assert np.array_equal(o["m"], outs[0]["m"])
+        assert np.abs(o["mz"] - outs[0]["mz"]).max() <= 1e-6
+    with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+        t = bt.autotune(reps=2)
+        assert t["gemm_tile_n"] in (128, 256) and t["stage_threads"] in (128, 256, 512)
+        assert t["gemm_ms"] > 0 and t["stage_ms"] > 0
+        bt.set_state(None, 0.0)
+        bt.advance(20)
+        assert np.array_equal(bt.read()["m"], outs[0]["m"])
