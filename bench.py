@@ -240,7 +240,9 @@ def main(args):
     prec = {"bf16x3": L.PREC_BF16X3, "fp32": L.PREC_FP32, "bf16": L.PREC_BF16}[args.precision]
     mesh, mats, hm, p = workload()
     B = args.islands
-    isl = synth.jittered_islands(B, seed=1, first_index=rank * B)
+    from paper_1603_09493_gb300 import shard
+    lo, _ = shard.island_range(B, rank)
+    isl = synth.jittered_islands(B, seed=1, first_index=lo)
     stream = torch.cuda.Stream()
     ctx = api.Context(local if world > 1 else 0, stream=stream)
     mid = ctx.mesh_upload(mesh, mats)
@@ -269,11 +271,8 @@ def main(args):
     e1.record(stream)
     e1.synchronize()
     clocks = sample_clocks_stop(proc, cf, local)
-    ms = e0.elapsed_time(e1)
+    ms = shard.max_over_ranks(e0.elapsed_time(e1), dist, device="cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
     out = bt.read()
@@ -327,10 +326,7 @@ def main(args):
         L.check(ctx.lib.bpm_run_batch(ctx.h, L.ptr(pin), B, __import__("ctypes").byref(q), args.steps,
                                       L.ptr(m_h), n, L.ptr(sw_h), L.ptr(ts_h), L.ptr(st_h)))
         el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = shard.max_over_ranks(el, dist, device="cuda")
         e2e = {"value": world * B * args.steps * DT_PS * 1e-3 / el, "unit": UNIT,
                "h2d_bytes_per_step": int(isl_arr.nbytes) / args.steps,
                "d2h_bytes_per_step": int(m_h.numel() * 4 + B * 9) / args.steps,

@@ -226,6 +226,11 @@ typedef struct {
 int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen);
 /* Apply a tuning (for example one cached from an earlier autotune). */
 int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t);
+/* Testing aid for the failure path: raise the batch's device error flag as a
+ * timed-out wait inside the tensor-core GEMM would (code != 0).  Later GEMM
+ * launches of the batch then return at once, and bpm_batch_read reports
+ * BPM_ERR_TIMEOUT.  code = 0 clears the flag. */
+int bpm_debug_set_gemm_error(bpm_batch* bt, int32_t code);
 /* Current simulated time of the batch. */
 int bpm_batch_time(bpm_batch* bt, double* t_ps);
 int bpm_batch_destroy(bpm_batch* bt);

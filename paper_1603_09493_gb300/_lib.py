@@ -81,6 +81,7 @@ PROTOTYPES = {
                                        POINTER(c_double)]),
     "bpm_batch_autotune": (c_int, [c_void_p, c_int32, POINTER(bpm_tuning)]),
     "bpm_batch_set_tuning": (c_int, [c_void_p, POINTER(bpm_tuning)]),
+    "bpm_debug_set_gemm_error": (c_int, [c_void_p, c_int32]),
     "bpm_batch_time": (c_int, [c_void_p, POINTER(c_double)]),
     "bpm_batch_destroy": (c_int, [c_void_p]),
     "bpm_run_batch": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,

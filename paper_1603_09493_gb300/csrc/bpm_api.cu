@@ -834,6 +834,17 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
     return BPM_OK;
 }
 
+int bpm_debug_set_gemm_error(bpm_batch* bt, int32_t code) {
+    if (!bt) {
+        set_error("null batch");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    BPM_CK(cudaMemcpyAsync(bt->gemm_err, &code, sizeof(int32_t), cudaMemcpyHostToDevice, bt->ctx->stream));
+    BPM_CK(cudaStreamSynchronize(bt->ctx->stream));
+    return BPM_OK;
+}
+
 int bpm_batch_time(bpm_batch* bt, double* t_ps) {
     if (!bt || !t_ps) {
         set_error("null argument");

@@ -1,0 +1,88 @@
+"""Failure detection without a GPU fault: every failure is made on the host
+(bad inputs, a NaN state, the GEMM error flag raised from the host) and must
+come back as an error code or a per-island status, with the context usable
+afterwards."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from paper_1603_09493_gb300 import _lib as L
+from paper_1603_09493_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not os.path.exists(L.LIB_PATH):
+        from paper_1603_09493_gb300 import build
+        build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def mid(ctx):
+    return ctx.mesh_upload(synth.small_island_mesh(), synth.ecc_materials())
+
+
+def test_bad_meshes_are_rejected(ctx):
+    m = synth.small_island_mesh()
+    bad = synth.IslandMesh(m.xyz_nm.copy(), m.tets.copy(), m.tet_region, m.z_interface_nm, m.height_nm)
+    bad.xyz_nm[bad.tets[0, 3]] = bad.xyz_nm[bad.tets[0, 0]]          # collapse tet 0
+    with pytest.raises(L.BpmError) as e:
+        ctx.mesh_upload(bad, synth.ecc_materials())
+    assert e.value.code == -1 and "degenerate" in str(e.value)
+    bad2 = synth.IslandMesh(m.xyz_nm, m.tets.copy(), m.tet_region, m.z_interface_nm, m.height_nm)
+    bad2.tets[5, 1] = m.n_nodes + 3
+    with pytest.raises(L.BpmError) as e:
+        ctx.mesh_upload(bad2, synth.ecc_materials())
+    assert e.value.code == -1
+    # the context still works
+    assert ctx.mesh_upload(m, synth.ecc_materials()) >= 0
+
+
+def test_bad_island_parameters_are_rejected(ctx, mid):
+    isl = synth.nominal_islands(4, mesh_id=mid)
+    isl.Ms_scale[2] = 0.0
+    with pytest.raises(L.BpmError) as e:
+        ctx.batch(isl, synth.RunParams(substeps=2), precision=L.PREC_BF16X3)
+    assert e.value.code == -1 and "Ms_scale" in str(e.value)
+    isl = synth.nominal_islands(4, mesh_id=mid + 100)
+    with pytest.raises(L.BpmError):
+        ctx.batch(isl, synth.RunParams(substeps=2))
+
+
+def test_nonfinite_island_is_flagged_alone(ctx, mid):
+    isl = synth.jittered_islands(6, seed=3, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, substeps=6, alpha=0.1, rise_ps=0.0, uniform_T=(0.0, 0.0, -0.5))
+    n = ctx.mesh_info(mid)["n_nodes"]
+    m0 = np.zeros((6, 3, n), np.float32)
+    m0[:, 2, :] = 1.0
+    m0[4, 0, 7] = np.nan
+    with ctx.batch(isl, p, precision=L.PREC_BF16X3) as bt:
+        bt.set_state(m0, 0.0)
+        bt.advance(5)
+        out = bt.read()
+    assert out["status"][4] & L.ISLAND_NONFINITE
+    assert np.all(out["status"][[0, 1, 2, 3, 5]] == 0)
+    assert np.all(np.isfinite(out["m"][[0, 1, 2, 3, 5]]))
+
+
+def test_gemm_error_flag_reports_timeout_and_clears(ctx, mid):
+    isl = synth.jittered_islands(8, seed=4, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, substeps=4, alpha=0.1)
+    with ctx.batch(isl, p, precision=L.PREC_BF16X3) as bt:
+        L.check(ctx.lib.bpm_debug_set_gemm_error(bt.h, 3))
+        bt.advance(2)                           # the GEMMs return at entry
+        with pytest.raises(L.BpmError) as e:
+            bt.read()
+        assert e.value.code == -4 and "gave up" in str(e.value)
+        L.check(ctx.lib.bpm_debug_set_gemm_error(bt.h, 0))
+        bt.set_state(None, 0.0)
+        bt.advance(2)
+        out = bt.read()
+        assert np.all(out["status"] == 0)
