@@ -69,12 +69,22 @@ __device__ __forceinline__ float3 eff_field(const StepArgs& a, int b, int i, flo
                                             float4 p1, float4 p2, float ramp, float xh, unsigned mask) {
     float3 B = f3(0, 0, 0);
     const int np = a.n_pad;
+    // independent per-node loads first, so that their latency overlaps the exchange gather
+    float3 hdv = f3(0, 0, 0);
+    if (mask & BPM_TERM_DEMAG) {
+        const float* hd = a.Hd + (size_t)b * 3 * np + i;
+        hdv = f3(hd[0], hd[np], hd[2 * np]);
+    }
+    const float4 pos = __ldg(a.node_pos + i);
+    const float an0 = __ldg(&a.node_mat[i].x);
     if (mask & BPM_TERM_EXCHANGE) {
         int s = i >> 5, l = i & 31;
         int off = __ldg(a.sell_off + s);
         int nw = (__ldg(a.sell_off + s + 1) - off) >> 5;
         const int2* ep = a.sell_ent + off + l;
         float bx = 0.f, by = 0.f, bz = 0.f;
+        // unrolled so that several entry loads are in flight (the loop is latency-bound)
+#pragma unroll 4
         for (int e = 0; e < nw; ++e) {
             int2 c = __ldg(ep + 32 * e);
             float v = __int_as_float(c.y);
@@ -86,15 +96,11 @@ __device__ __forceinline__ float3 eff_field(const StepArgs& a, int b, int i, flo
     }
     if (mask & BPM_TERM_ANISOTROPY) {
         float3 u = f3(p1.x, p1.y, p1.z);
-        float an = __ldg(&a.node_mat[i].x) * p0.y;
+        float an = an0 * p0.y;
         B = B + (an * dot3(mi, u)) * u;
     }
-    if (mask & BPM_TERM_DEMAG) {
-        const float* hd = a.Hd + (size_t)b * 3 * np + i;
-        B = B + f3(hd[0], hd[np], hd[2 * np]);
-    }
+    if (mask & BPM_TERM_DEMAG) B = B + hdv;
     if ((mask & BPM_TERM_HEAD) && a.map) {
-        float4 pos = __ldg(a.node_pos + i);
         B = B + ramp * trilinear(a, pos.x + p1.w - xh, pos.y + p2.x, pos.z);
     }
     if (mask & BPM_TERM_UNIFORM) {
@@ -196,10 +202,10 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_stage2(StepArgs a, int j) {
     float mzp = 0.f;
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
+        const float3 mn = f3(a.m[base + i], a.m[base + np + i], a.m[base + 2 * np + i]);
+        const float3 f1 = f3(a.k1[base + i], a.k1[base + np + i], a.k1[base + 2 * np + i]);
         float3 B = eff_field(a, b, i, mi, sm, p0, p1, p2, ramp, xh, a.mask);
         float3 f2 = llg_rhs(mi, B, a.alpha, a.gp);
-        float3 mn = f3(a.m[base + i], a.m[base + np + i], a.m[base + 2 * np + i]);
-        float3 f1 = f3(a.k1[base + i], a.k1[base + np + i], a.k1[base + 2 * np + i]);
         float3 v = normalize3(mn + hh * (f1 + f2));
         a.m[base + i] = v.x;
         a.m[base + np + i] = v.y;
