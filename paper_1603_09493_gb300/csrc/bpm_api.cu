@@ -52,6 +52,7 @@ struct bpm_batch {
     std::vector<cudaStream_t> side;   // fork streams for the groups of a multi-mesh batch
     std::vector<cudaEvent_t> ev;
     int tile_n = 256;                 // demag GEMM output columns per CTA
+    GroupedGemm gg;                   // tensor-core demag GEMM over all groups (BF16 precisions)
 };
 
 namespace {
@@ -77,7 +78,25 @@ Mesh* get_mesh(bpm_ctx* ctx, int id) {
     return ctx->meshes[id];
 }
 
-// demag GEMM of a group's current operand A -> Hd
+bool tensor_core_precision(const bpm_batch* bt) {
+    return bt->p.precision == BPM_PREC_BF16X3 || bt->p.precision == BPM_PREC_BF16;
+}
+
+// (re)encode the grouped tensor-core GEMM of the batch for its current tile width
+int setup_grouped_gemm(bpm_batch* bt) {
+    std::vector<GemmOperands> ops;
+    for (auto& g : bt->groups) {
+        const int K = g.mesh->K();
+        ops.push_back(GemmOperands{g.Ahi, g.Alo, g.mesh->Nhi, g.mesh->Nlo, g.Hd, g.Bp, K, K});
+    }
+    return grouped_gemm_setup(&bt->gg, ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1);
+}
+
+// demag GEMM of every group's current operand A -> Hd: one persistent launch
+// on the tensor cores, or one CUDA-core launch per group
+int run_demag_all(bpm_batch* bt, cudaStream_t s);
+
+// demag GEMM of a group's current operand A -> Hd (CUDA-core precisions)
 int run_demag_gemm(bpm_batch* bt, Group& g, cudaStream_t s) {
     Mesh* M = g.mesh;
     const int K = M->K();
@@ -86,14 +105,16 @@ int run_demag_gemm(bpm_batch* bt, Group& g, cudaStream_t s) {
             return gemm_f32_nt(s, g.Bp, K, K, g.A32, K, M->N32, K, g.Hd, K);
         case BPM_PREC_BF16X3_REF:
             return gemm_bf16x3_simt(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 3);
-        case BPM_PREC_BF16X3:
-            return gemm_bf16x3_tc(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 3, bt->gemm_err, bt->tile_n);
-        case BPM_PREC_BF16:
-            return gemm_bf16x3_tc(s, g.Bp, K, K, g.Ahi, g.Alo, M->Nhi, M->Nlo, g.Hd, 1, bt->gemm_err, bt->tile_n);
         default:
             set_error("unknown precision %d", bt->p.precision);
             return BPM_ERR_ARG;
     }
+}
+
+int run_demag_all(bpm_batch* bt, cudaStream_t s) {
+    if (tensor_core_precision(bt)) return grouped_gemm_launch(s, bt->gg, bt->ctx->sm_count, bt->gemm_err);
+    for (auto& g : bt->groups) BPM_TRY(run_demag_gemm(bt, g, s));
+    return BPM_OK;
 }
 
 int enqueue_group_interval(bpm_batch* bt, Group& g, cudaStream_t s) {
@@ -106,10 +127,76 @@ int enqueue_group_interval(bpm_batch* bt, Group& g, cudaStream_t s) {
     return BPM_OK;
 }
 
+// Stage launches of a multi-group batch: the groups, largest mesh first, cut into
+// classes within which every group keeps the resident CTAs per SM it would have
+// in a launch of its own (the class's shared memory is its largest group's).
+struct StageLaunches {
+    std::vector<StageGroups> launch;
+    std::vector<size_t> smem;
+    int threads = 256;
+};
+
+int build_stage_launches(const bpm_batch* bt, StageLaunches* out) {
+    out->launch.clear();
+    out->smem.clear();
+    out->threads = bt->groups[0].args.threads;
+    std::vector<int> order(bt->groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return bt->groups[x].mesh->n_pad > bt->groups[y].mesh->n_pad;
+    });
+    int class_occ = -1;
+    for (int gi : order) {
+        const Group& g = bt->groups[gi];
+        const size_t sb = stage_smem_bytes(g.args);
+        int occ = 0;
+        BPM_TRY(stage_blocks_per_sm(out->threads, sb, &occ));
+        if (out->launch.empty() || occ != class_occ || out->launch.back().ng == kMaxStageGroups) {
+            out->launch.emplace_back();
+            std::memset(&out->launch.back(), 0, sizeof(StageGroups));
+            out->smem.push_back(sb);
+            class_occ = occ;
+        }
+        StageGroups& G = out->launch.back();
+        G.a[G.ng] = g.args;
+        G.block_begin[G.ng + 1] = G.block_begin[G.ng] + g.B;
+        ++G.ng;
+    }
+    return BPM_OK;
+}
+
+// Heun stage (1 or 2) of every group: one launch per group of a single-group
+// batch, one launch per class otherwise
+void launch_stage_all(bpm_batch* bt, const StageLaunches& L, int stage, int j, cudaStream_t s) {
+    if (bt->groups.size() == 1) {
+        if (stage == 1)
+            launch_stage1(bt->groups[0].args, j, s);
+        else
+            launch_stage2(bt->groups[0].args, j, s);
+        return;
+    }
+    for (size_t c = 0; c < L.launch.size(); ++c) {
+        if (stage == 1)
+            launch_stage1_groups(L.launch[c], L.threads, L.smem[c], j, s);
+        else
+            launch_stage2_groups(L.launch[c], L.threads, L.smem[c], j, s);
+    }
+}
+
 // one output interval of every group; groups of a multi-mesh batch are forked
 // over side streams so that their kernels can run concurrently
 int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
-    if (bt->groups.size() == 1) {
+    if (tensor_core_precision(bt)) {
+        // one grouped GEMM launch and one stage launch per class per Heun stage
+        StageLaunches L;
+        if (bt->groups.size() > 1) BPM_TRY(build_stage_launches(bt, &L));
+        for (int j = 0; j < bt->p.substeps; ++j) {
+            BPM_TRY(run_demag_all(bt, s));
+            launch_stage_all(bt, L, 1, j, s);
+            BPM_TRY(run_demag_all(bt, s));
+            launch_stage_all(bt, L, 2, j, s);
+        }
+    } else if (bt->groups.size() == 1) {
         BPM_TRY(enqueue_group_interval(bt, bt->groups[0], s));
     } else {
         const int ns = (int)bt->side.size();
@@ -148,6 +235,7 @@ void free_batch(bpm_batch* bt) {
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     if (bt->graph) cudaGraphDestroy(bt->graph);
     for (auto& g : bt->groups) free_group(g);
+    grouped_gemm_free(&bt->gg);
     cudaFree(bt->gemm_err);
     cudaFree(bt->interval);
     for (auto s : bt->side) cudaStreamDestroy(s);
@@ -521,6 +609,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
             if (r == BPM_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) r = BPM_ERR_CUDA;
         if (r != BPM_OK) set_error("stream/event creation failed");
     }
+    if (r == BPM_OK && tensor_core_precision(bt)) r = setup_grouped_gemm(bt);
     if (r != BPM_OK) {
         free_batch(bt);
         return r;
@@ -714,7 +803,9 @@ int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out
         BPM_CK(cudaMemsetAsync(dout, 0, user_bytes, s));
     }
     int r = BPM_OK;
+    if (term_mask & BPM_TERM_DEMAG) r = run_demag_all(bt, s);
     for (auto& g : bt->groups) {
+        if (r != BPM_OK) break;
         const int n = g.mesh->n, np = g.mesh->n_pad;
         float* tmp = nullptr;
         cudaError_t e = cudaMallocAsync(&tmp, (size_t)g.Bp * 3 * np * sizeof(float), s);
@@ -723,7 +814,6 @@ int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out
             r = BPM_ERR_OOM;
             break;
         }
-        if (term_mask & BPM_TERM_DEMAG) r = run_demag_gemm(bt, g, s);
         if (r == BPM_OK) {
             launch_field(g.args, t_ps, term_mask, tmp, s);
             k_scatter_state<<<dim3((n + 255) / 256, 3 * g.B), 256, 0, s>>>(n, np, ld, g.d_idx, tmp, dout);
@@ -754,31 +844,37 @@ int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double*
     cudaEvent_t ev[5];
     for (auto& e : ev) BPM_CK(cudaEventCreate(&e));
     double acc[3] = {0, 0, 0};
-    int r = BPM_OK;
+    StageLaunches L;
+    int r = bt->groups.size() > 1 && tensor_core_precision(bt) ? build_stage_launches(bt, &L) : BPM_OK;
+    auto stage = [&](int k, int j) {
+        if (tensor_core_precision(bt)) {
+            launch_stage_all(bt, L, k, j, s);
+            return;
+        }
+        for (auto& g : bt->groups) (k == 1 ? launch_stage1 : launch_stage2)(g.args, j, s);
+    };
     for (int q = 0; q < reps && r == BPM_OK; ++q) {
         int j = q % bt->p.substeps;
-        for (auto& g : bt->groups) {
-            cudaEventRecord(ev[0], s);
-            r = run_demag_gemm(bt, g, s);
-            cudaEventRecord(ev[1], s);
-            launch_stage1(g.args, j, s);
-            cudaEventRecord(ev[2], s);
-            if (r == BPM_OK) r = run_demag_gemm(bt, g, s);
-            cudaEventRecord(ev[3], s);
-            launch_stage2(g.args, j, s);
-            cudaEventRecord(ev[4], s);
-            cudaError_t e = cudaEventSynchronize(ev[4]);
-            if (e != cudaSuccess) {
-                set_error("kernel timing: %s", cudaGetErrorString(e));
-                r = BPM_ERR_CUDA;
-                break;
-            }
-            float t[4];
-            for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
-            acc[0] += 0.5 * (t[0] + t[2]);
-            acc[1] += t[1];
-            acc[2] += t[3];
+        cudaEventRecord(ev[0], s);
+        r = run_demag_all(bt, s);
+        cudaEventRecord(ev[1], s);
+        stage(1, j);
+        cudaEventRecord(ev[2], s);
+        if (r == BPM_OK) r = run_demag_all(bt, s);
+        cudaEventRecord(ev[3], s);
+        stage(2, j);
+        cudaEventRecord(ev[4], s);
+        cudaError_t e = cudaEventSynchronize(ev[4]);
+        if (e != cudaSuccess) {
+            set_error("kernel timing: %s", cudaGetErrorString(e));
+            r = BPM_ERR_CUDA;
+            break;
         }
+        float t[4];
+        for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
+        acc[0] += 0.5 * (t[0] + t[2]);
+        acc[1] += t[1];
+        acc[2] += t[3];
     }
     for (auto& e : ev) cudaEventDestroy(e);
     if (r != BPM_OK) return r;
@@ -799,6 +895,7 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
     bt->tile_n = t->gemm_tile_n;
     for (auto& g : bt->groups) g.args.threads = t->stage_threads;
     drop_graph(bt);   // the graph holds the old launch configurations
+    if (tensor_core_precision(bt)) BPM_TRY(setup_grouped_gemm(bt));
     return BPM_OK;
 }
 

@@ -1,0 +1,279 @@
+// Persistent, grouped demag GEMM on the tensor cores (tcgen05, sm_103a).
+//
+// One launch computes, for every mesh group g of a batch (uneven mesh sizes),
+//   C_g[M_g][N_g] = sum of the BF16 split products of A_g[M_g][K_g] and W_g[N_g][K_g]^T
+// (3 products hi*hi + lo*hi + hi*lo, or 1), FP32 accumulate in TMEM.  The
+// 128 x TN output tiles of all groups form one list; each CTA (one per SM)
+// walks it with a stride of the grid size.  Warp roles:
+//   warp 0  one lane streams the k-blocks of every tile with TMA into a ring of
+//           shared-memory stages (the ring runs across tile boundaries);
+//   warp 1  allocates two TMEM accumulators; one lane issues the MMAs, tile i
+//           into accumulator i % 2;
+//   warps 2-5  read an accumulator back (tcgen05.ld) and store it, while the
+//           MMAs of the next tile run into the other accumulator.
+// Per-group tensor maps live in a device array (64-byte aligned entries).
+// Every wait is bounded; on timeout the kernel raises the error flag, drains
+// its copies and MMAs, frees TMEM and exits, and later launches return at once.
+#include <cstring>
+
+#include "bpm_tc_ptx.cuh"
+
+namespace bpm {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kGThreads = 192;
+
+template <int P, int TN>
+struct GCfg {
+    static constexpr int W_TILE = Tile<TN>::W_TILE;
+    static constexpr int stage_bytes = (P == 3 ? 2 : 1) * (A_TILE + W_TILE);
+    static constexpr int stages = (192 * 1024) / stage_bytes;
+    static constexpr int smem = stages * stage_bytes + 1024 + 256;
+};
+
+__device__ __forceinline__ int find_group(const GemmGroupDev* __restrict__ G, int ng, int t) {
+    int g = 0;
+    while (g + 1 < ng && t >= G[g + 1].tile_begin) ++g;
+    return g;
+}
+
+template <int P, int TN>
+__global__ void __launch_bounds__(kGThreads, 1)
+    k_gemm_grouped(const GemmGroupDev* __restrict__ G, int ng, int total_tiles, int* err) {
+    using CF = GCfg<P, TN>;
+    constexpr int S = CF::stages;
+    constexpr int W_TILE = CF::W_TILE;
+    extern __shared__ uint8_t smem_raw[];
+    {   // an earlier launch gave up: skip (decided once per CTA, so that no thread is left at a barrier)
+        __shared__ int s_abort;
+        if (threadIdx.x == 0) s_abort = *(volatile int*)err;
+        __syncthreads();
+        if (s_abort) return;
+    }
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t bar0 = base + S * CF::stage_bytes;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+    auto accf_bar = [&](int a) { return bar0 + 8u * (2 * S + a); };
+    auto acce_bar = [&](int a) { return bar0 + 8u * (2 * S + 2 + a); };
+    const uint32_t done_bar = bar0 + 8u * (2 * S + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * CF::stage_bytes + 8 * (2 * S + 5));
+    auto sAhi = [&](int s) { return base + s * CF::stage_bytes; };
+    auto sWhi = [&](int s) { return base + s * CF::stage_bytes + A_TILE; };
+    auto sAlo = [&](int s) { return base + s * CF::stage_bytes + A_TILE + W_TILE; };
+    auto sWlo = [&](int s) { return base + s * CF::stage_bytes + 2 * A_TILE + W_TILE; };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf_bar(a), 1);
+            mbar_init(acce_bar(a), 4);     // one arrival per epilogue warp
+        }
+        mbar_init(done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int kbg = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+            const int g = find_group(G, ng, t);
+            const GemmGroupDev& gg = G[g];
+            const int lt = t - gg.tile_begin;
+            const int m0 = (lt / gg.tiles_n) * TM, n0 = (lt % gg.tiles_n) * TN;
+            const int nk = gg.K / TK;
+            for (int kb = 0; kb < nk; ++kb, ++kbg) {
+                const int s = kbg % S;
+                if (kbg >= S) ok = mbar_wait(empty_bar(s), ((kbg / S) - 1) & 1, err, 11);
+                if (!ok) break;
+                mbar_expect_tx(full_bar(s), CF::stage_bytes);
+                const int kc = kb * TK;
+                tma_load_2d(sAhi(s), &gg.ahi, kc, m0, full_bar(s));
+                tma_load_2d(sWhi(s), &gg.whi, kc, n0, full_bar(s));
+                if (P == 3) {
+                    tma_load_2d(sAlo(s), &gg.alo, kc, m0, full_bar(s));
+                    tma_load_2d(sWlo(s), &gg.wlo, kc, n0, full_bar(s));
+                }
+            }
+        }
+        // drain: the last armed phase of every stage must land before exit
+        const int armed = kbg;
+        for (int k = (armed > S ? armed - S : 0); k < armed; ++k) mbar_drain(full_bar(k % S), (k / S) & 1, err, 12);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        int kbg = 0, i = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++i) {
+            const int g = find_group(G, ng, t);
+            const int nk = G[g].K / TK;
+            const int a = i & 1;
+            if (i >= 2) ok = mbar_wait(acce_bar(a), ((i >> 1) - 1) & 1, err, 13);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)(a * TN);
+            for (int kb = 0; kb < nk; ++kb, ++kbg) {
+                const int s = kbg % S;
+                ok = mbar_wait(full_bar(s), (kbg / S) & 1, err, 14);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int k = 0; k < TK / 16; ++k) {
+                    const uint32_t koff = 32u * k;
+                    const uint64_t ahi = sw128_desc(sAhi(s) + koff), whi = sw128_desc(sWhi(s) + koff);
+                    mma_bf16<TN>(acc, ahi, whi, (kb > 0 || k > 0) ? 1u : 0u);
+                    if (P == 3) {
+                        const uint64_t alo = sw128_desc(sAlo(s) + koff), wlo = sw128_desc(sWlo(s) + koff);
+                        mma_bf16<TN>(acc, alo, whi, 1u);
+                        mma_bf16<TN>(acc, ahi, wlo, 1u);
+                    }
+                }
+                mma_commit(empty_bar(s));
+            }
+            if (ok) mma_commit(accf_bar(a));
+        }
+        mma_commit(done_bar);      // tracks every MMA issued above, also on the error path
+    } else if (warp >= 2) {
+        // ---------------- epilogue warps ----------------
+        const int q = warp & 3;    // TMEM lane quarter this warp may access
+        int i = 0;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
+            const int g = find_group(G, ng, t);
+            const GemmGroupDev& gg = G[g];
+            const int lt = t - gg.tile_begin;
+            const int m0 = (lt / gg.tiles_n) * TM, n0 = (lt % gg.tiles_n) * TN;
+            const int a = i & 1;
+            const bool have = mbar_wait(accf_bar(a), (i >> 1) & 1, err, 15);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int go = __shfl_sync(0xffffffffu, (have && *(volatile int*)err == 0) ? 1 : 0, 0);
+            if (!go) break;
+            const int row = m0 + q * 32 + lane;
+            const uint32_t lane_addr = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < TN; c += 32) {
+                uint32_t r[32];
+                tmem_ld32(lane_addr + (uint32_t)c, r);
+                const int col = n0 + c;
+                if (row < gg.M && col < gg.N) {
+                    float4* dst = reinterpret_cast<float4*>(gg.C + (size_t)row * gg.ldc + col);
+#pragma unroll
+                    for (int v = 0; v < 8; ++v)
+                        if (col + 4 * v < gg.N)
+                            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                                 __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce_bar(a));
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        mbar_drain(done_bar, 0, err, 16);     // every MMA has completed before TMEM is released
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN) : "memory");
+    }
+}
+
+template <int P, int TN>
+int launch_grouped(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err) {
+    static bool configured = false;
+    if (!configured) {
+        BPM_CK(cudaFuncSetAttribute(k_gemm_grouped<P, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    GCfg<P, TN>::smem));
+        configured = true;
+    }
+    const int grid = std::max(1, std::min(gg.total_tiles, sm_count));
+    k_gemm_grouped<P, TN><<<grid, kGThreads, GCfg<P, TN>::smem, s>>>(gg.d_groups, gg.n_groups, gg.total_tiles, err);
+    BPM_CK(cudaGetLastError());
+    return BPM_OK;
+}
+
+}  // namespace
+
+int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products) {
+    if (tile_n != 128 && tile_n != 256) {
+        set_error("grouped GEMM tile width must be 128 or 256");
+        return BPM_ERR_ARG;
+    }
+    std::vector<GemmGroupDev> h(ops.size());
+    int tiles = 0;
+    for (size_t g = 0; g < ops.size(); ++g) {
+        const GemmOperands& o = ops[g];
+        if (o.M % tc::TM || o.K % tc::TK || o.N % 16 || o.M <= 0 || o.N <= 0) {
+            set_error("grouped GEMM group %zu: M %% 128, K %% 64, N %% 16 required (M=%d N=%d K=%d)", g, o.M, o.N,
+                      o.K);
+            return BPM_ERR_ARG;
+        }
+        std::memset(&h[g], 0, sizeof(GemmGroupDev));
+        BPM_TRY(make_bf16_tensor_map(&h[g].ahi, o.Ahi, o.K, o.M, tc::TM));
+        BPM_TRY(make_bf16_tensor_map(&h[g].whi, o.Whi, o.K, o.N, tile_n));
+        if (products == 3) {
+            BPM_TRY(make_bf16_tensor_map(&h[g].alo, o.Alo, o.K, o.M, tc::TM));
+            BPM_TRY(make_bf16_tensor_map(&h[g].wlo, o.Wlo, o.K, o.N, tile_n));
+        } else {
+            h[g].alo = h[g].ahi;
+            h[g].wlo = h[g].whi;
+        }
+        h[g].C = o.C;
+        h[g].M = o.M;
+        h[g].N = o.N;
+        h[g].K = o.K;
+        h[g].ldc = o.N;
+        h[g].tiles_n = (o.N + tile_n - 1) / tile_n;
+        h[g].tile_begin = tiles;
+        tiles += (o.M / tc::TM) * h[g].tiles_n;
+    }
+    grouped_gemm_free(gg);
+    BPM_CK(cudaMalloc(&gg->d_groups, h.size() * sizeof(GemmGroupDev)));
+    BPM_CK(cudaMemcpy(gg->d_groups, h.data(), h.size() * sizeof(GemmGroupDev), cudaMemcpyHostToDevice));
+    gg->n_groups = (int)h.size();
+    gg->total_tiles = tiles;
+    gg->tile_n = tile_n;
+    gg->products = products;
+    return BPM_OK;
+}
+
+void grouped_gemm_free(GroupedGemm* gg) {
+    if (gg->d_groups) cudaFree(gg->d_groups);
+    gg->d_groups = nullptr;
+    gg->n_groups = gg->total_tiles = 0;
+}
+
+int grouped_gemm_launch(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err) {
+    if (!gg.d_groups) {
+        set_error("grouped GEMM not set up");
+        return BPM_ERR_STATE;
+    }
+    if (gg.products == 3) {
+        if (gg.tile_n == 128) return launch_grouped<3, 128>(s, gg, sm_count, err);
+        return launch_grouped<3, 256>(s, gg, sm_count, err);
+    }
+    if (gg.tile_n == 128) return launch_grouped<1, 128>(s, gg, sm_count, err);
+    return launch_grouped<1, 256>(s, gg, sm_count, err);
+}
+
+}  // namespace bpm

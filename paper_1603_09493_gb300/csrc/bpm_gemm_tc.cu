@@ -1,10 +1,8 @@
-// Demag GEMM on the 5th-generation tensor cores (tcgen05, sm_103a):
-//   C[M][N] = sum over products of A_x[M][K] * W_y[N][K]^T,  FP32 accumulate in TMEM,
-// with the BF16 hi/lo split of both operands:
-//   products = 3: Ahi*Whi + Alo*Whi + Ahi*Wlo   (the lo*lo term, ~2^-16 relative, is dropped)
-//   products = 1: Ahi*Whi
-// A is the demag source Ms*m of the batch ([M] islands x [K] = 3 n_pad, K-major), W the
-// demag operator (row = output node/component, K-major).
+// Tensor-core GEMM with fused epilogues (tcgen05, sm_103a), used by the surrogate MLP:
+//   C[M][N] = A[M][K] * W[N][K]^T, BF16 operands, FP32 accumulate in TMEM
+// (the kernel also supports the BF16 hi/lo split, products = 3: Ahi*Whi + Alo*Whi +
+// Ahi*Wlo; the batched demag product uses the persistent grouped kernel in
+// bpm_gemm_grouped.cu).
 //
 // One CTA computes a 128 x 256 output tile.  Warp 0 (one elected lane) streams the
 // k-blocks (64 BF16 = one 128-byte swizzle atom) of every operand tile with TMA into a
@@ -16,124 +14,15 @@
 // kernel records an error flag, drains its own copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
 
-#include "bpm_internal.cuh"
+#include "bpm_tc_ptx.cuh"
 
 namespace bpm {
 
 namespace {
 
-constexpr int TM = 128, TK = 64;           // output rows per CTA; TK = one 128 B swizzle row of BF16
-constexpr int A_TILE = TM * TK * 2;         // 16 KB
-template <int TN>
-struct Tile {
-    static constexpr int W_TILE = TN * TK * 2;   // 32 KB (TN = 256) or 16 KB (TN = 128)
-};
-constexpr unsigned long long kWaitNs = 200000000ull;      // 200 ms per wait (a normal wait is < 0.1 ms)
+using namespace tc;
+
 constexpr int kThreads = 128;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// bounded wait: returns false (and raises the error flag) if the phase does not complete
-// within kWaitNs, or as soon as another CTA has raised the flag
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        for (int i = 0; i < 256; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs || *(volatile int*)err != 0) break;
-    }
-    atomicExch(err, code);
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
-}
-
-// shared-memory matrix descriptor: K-major operand tile written by TMA with 128 B swizzle
-// (rows of 128 B, 8-row groups 1024 B apart); start address advances 32 B per K=16 slice
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);       // start address
-    d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                        // 128 B swizzle
-    return d;
-}
-
-// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128, N = TN
-template <int TN>
-struct Idesc {
-    static constexpr uint32_t value = (1u << 4)              // D = F32
-                                      | (1u << 7)            // A = BF16
-                                      | (1u << 10)           // B = BF16
-                                      | ((uint32_t)(TN >> 3) << 17)
-                                      | ((uint32_t)(TM >> 4) << 24);
-};
-
-template <int TN>
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-        "}\n" ::"r"(tmem),
-        "l"(adesc), "l"(bdesc), "r"(Idesc<TN>::value), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 template <int P, int TN>
 struct Cfg {
@@ -225,7 +114,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * TN, m0 = blockIdx.y * TM;
     const int nk = K / TK;
-    if (*(volatile int*)err != 0) return;      // an earlier launch gave up: results are invalid anyway
+    {   // an earlier launch gave up: skip (decided once per CTA, so that no thread is left at a barrier)
+        __shared__ int s_abort;
+        if (threadIdx.x == 0) s_abort = *(volatile int*)err;
+        __syncthreads();
+        if (s_abort) return;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -271,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         // drain: every stage armed so far must have landed before the CTA may exit
         for (int kb = (issued > S ? issued - S : 0); kb < issued; ++kb)
-            mbar_wait(full_bar(kb % S), (kb / S) & 1, err, 2);
+            mbar_drain(full_bar(kb % S), (kb / S) & 1, err, 2);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         bool ok = true;
@@ -297,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
     // ---------------- epilogue: TMEM -> registers -> global ----------------
-    const bool have = mbar_wait(done_bar, 0, err, 4);
+    const bool have = mbar_drain(done_bar, 0, err, 4);   // also on the error path: MMAs land before TMEM is freed
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // tcgen05.ld is warp-collective: take the decision once per warp
     const int go = __shfl_sync(0xffffffffu, (have && *(volatile int*)err == 0) ? 1 : 0, 0);
@@ -326,15 +220,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
+        __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
     }
 }
+
+template <int P, int EPI, int TN = 256>
+int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
+           const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, const TcEpilogue& e, int* err) {
+    static bool configured = false;
+    if (!configured) {
+        BPM_CK(cudaFuncSetAttribute(k_gemm_tc<P, EPI, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Cfg<P, TN>::smem));
+        configured = true;
+    }
+    CUtensorMap mAhi, mAlo, mWhi, mWlo;
+    BPM_TRY(make_bf16_tensor_map(&mAhi, Ahi, K, M, TM));
+    BPM_TRY(make_bf16_tensor_map(&mWhi, Whi, K, N, TN));
+    if (P == 3) {
+        BPM_TRY(make_bf16_tensor_map(&mAlo, Alo, K, M, TM));
+        BPM_TRY(make_bf16_tensor_map(&mWlo, Wlo, K, N, TN));
+    } else {
+        mAlo = mAhi;
+        mWlo = mWhi;
+    }
+    dim3 grid((N + TN - 1) / TN, M / TM);
+    k_gemm_tc<P, EPI, TN><<<grid, kThreads, Cfg<P, TN>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, e, err);
+    BPM_CK(cudaGetLastError());
+    return BPM_OK;
+}
+
+}  // namespace
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-EncodeTiledFn encode_fn() {
+static EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         void* p = nullptr;
@@ -347,7 +269,7 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-int make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows) {
+int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -369,56 +291,6 @@ int make_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_row
         return BPM_ERR_CUDA;
     }
     return BPM_OK;
-}
-
-template <int P, int EPI, int TN = 256>
-int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
-           const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, const TcEpilogue& e, int* err) {
-    static bool configured = false;
-    if (!configured) {
-        BPM_CK(cudaFuncSetAttribute(k_gemm_tc<P, EPI, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    Cfg<P, TN>::smem));
-        configured = true;
-    }
-    CUtensorMap mAhi, mAlo, mWhi, mWlo;
-    BPM_TRY(make_map(&mAhi, Ahi, K, M, TM));
-    BPM_TRY(make_map(&mWhi, Whi, K, N, TN));
-    if (P == 3) {
-        BPM_TRY(make_map(&mAlo, Alo, K, M, TM));
-        BPM_TRY(make_map(&mWlo, Wlo, K, N, TN));
-    } else {
-        mAlo = mAhi;
-        mWlo = mWhi;
-    }
-    dim3 grid((N + TN - 1) / TN, M / TM);
-    k_gemm_tc<P, EPI, TN><<<grid, kThreads, Cfg<P, TN>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, e, err);
-    BPM_CK(cudaGetLastError());
-    return BPM_OK;
-}
-
-}  // namespace
-
-int gemm_bf16x3_tc(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
-                   const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo, float* C, int products, int* err_flag,
-                   int tile_n) {
-    if (M % TM || K % TK || N % 16 || M <= 0 || N <= 0) {
-        set_error("tensor-core GEMM needs M %% %d == 0, K %% %d == 0, N %% 16 == 0 (M=%d N=%d K=%d)", TM, TK, M, N, K);
-        return BPM_ERR_ARG;
-    }
-    TcEpilogue e{};
-    e.C = C;
-    e.ldc = N;
-    e.rows_valid = M;
-    e.cols_valid = N;
-    if (tile_n == 128) {
-        if (products == 3) return launch<3, TC_EPI_STORE, 128>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
-        if (products == 1) return launch<1, TC_EPI_STORE, 128>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
-    } else {
-        if (products == 3) return launch<3, TC_EPI_STORE, 256>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
-        if (products == 1) return launch<1, TC_EPI_STORE, 256>(s, M, N, K, Ahi, Alo, Whi, Wlo, e, err_flag);
-    }
-    set_error("products must be 1 or 3");
-    return BPM_ERR_ARG;
 }
 
 int gemm_tc(cudaStream_t s, int epi, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* W,

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libbpmllg.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -113,14 +114,33 @@ struct TcEpilogue {
 int gemm_tc(cudaStream_t s, int epi, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* W,
             const TcEpilogue& e, int* err_flag);
 
+// grouped persistent tensor-core GEMM (bpm_gemm_grouped.cu): one launch over the
+// output tiles of every mesh group of a batch
+struct GemmGroupDev {   // CUtensorMap members carry the 64-byte alignment TMA needs
+    CUtensorMap ahi, alo, whi, wlo;   // 128 B each, 64-byte aligned
+    float* C;
+    int M, N, K, ldc;
+    int tiles_n, tile_begin;          // N tiles of this group; first tile in the global list
+};
+struct GemmOperands {
+    const __nv_bfloat16 *Ahi, *Alo, *Whi, *Wlo;
+    float* C;
+    int M, N, K;
+};
+struct GroupedGemm {
+    GemmGroupDev* d_groups = nullptr;
+    int n_groups = 0, total_tiles = 0, tile_n = 256, products = 3;
+};
+int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products);
+void grouped_gemm_free(GroupedGemm* gg);
+int grouped_gemm_launch(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err);
+int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows);
+
 // demag GEMMs: C[M_rows][Nout] = A[M_rows][K] * W[Nout][K]^T, row strides lda/ldw/ldc (elements)
 int gemm_f32_nt(cudaStream_t s, int M_rows, int Nout, int K, const float* A, int lda,
                 const float* W, int ldw, float* C, int ldc);
 int gemm_bf16x3_simt(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi,
                      const __nv_bfloat16* Alo, const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo,
                      float* C, int products);
-int gemm_bf16x3_tc(cudaStream_t s, int M_rows, int Nout, int K, const __nv_bfloat16* Ahi,
-                   const __nv_bfloat16* Alo, const __nv_bfloat16* Whi, const __nv_bfloat16* Wlo,
-                   float* C, int products, int* err_flag, int tile_n);
 
 }  // namespace bpm

@@ -16,6 +16,7 @@
 // or BF16 hi/lo).  Stage 2 also updates the volume-averaged
 // <m_z> switch detector with a fixed-order block reduction.  The demag field of
 // the stage's source state comes from the GEMM that ran just before the stage.
+#include <algorithm>
 #include <cmath>
 
 #include "bpm_step.cuh"
@@ -154,12 +155,10 @@ __device__ __forceinline__ double step_time(const StepArgs& a, int j) {
     return a.t0 + (double)(it * a.k + j) * a.h;
 }
 
-// occupancy bound: 1536 resident threads per SM (at most 40 registers each)
-template <int NT>
-__global__ void __launch_bounds__(NT, 1536 / NT) k_stage1(StepArgs a, int j) {
+// predictor of island b (one CTA)
+__device__ __forceinline__ void stage1_body(const StepArgs& a, int b, int j) {
     extern __shared__ float4 smem4[];
     float* sm = reinterpret_cast<float*>(smem4);
-    const int b = blockIdx.x;
     const int np = a.n_pad;
     const size_t base = (size_t)b * 3 * np;
     const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
@@ -184,12 +183,10 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_stage1(StepArgs a, int j) {
     }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, 1536 / NT) k_stage2(StepArgs a, int j) {
+// corrector and switch detector of island b (one CTA); red: one float per warp
+__device__ __forceinline__ void stage2_body(const StepArgs& a, int b, int j, float* red) {
     extern __shared__ float4 smem4[];
-    __shared__ float red[NT / 32];
     float* sm = reinterpret_cast<float*>(smem4);
-    const int b = blockIdx.x;
     const int np = a.n_pad;
     const size_t base = (size_t)b * 3 * np;
     const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
@@ -225,6 +222,38 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_stage2(StepArgs a, int j) {
         a.mz_prev[b] = mz;
         if (!isfinite(mz)) a.status[b] |= BPM_ISLAND_NONFINITE;
     }
+}
+
+// occupancy bound: 1536 resident threads per SM (at most 40 registers each)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1536 / NT) k_stage1(StepArgs a, int j) {
+    stage1_body(a, blockIdx.x, j);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1536 / NT) k_stage2(StepArgs a, int j) {
+    __shared__ float red[NT / 32];
+    stage2_body(a, blockIdx.x, j, red);
+}
+
+// group of CTA blockIdx.x in a launch over several mesh groups
+__device__ __forceinline__ int stage_group(const StageGroups& G) {
+    int g = 0;
+    while (g + 1 < G.ng && (int)blockIdx.x >= G.block_begin[g + 1]) ++g;
+    return g;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1536 / NT) k_stage1_groups(const __grid_constant__ StageGroups G, int j) {
+    const int g = stage_group(G);
+    stage1_body(G.a[g], blockIdx.x - G.block_begin[g], j);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1536 / NT) k_stage2_groups(const __grid_constant__ StageGroups G, int j) {
+    __shared__ float red[NT / 32];
+    const int g = stage_group(G);
+    stage2_body(G.a[g], blockIdx.x - G.block_begin[g], j, red);
 }
 
 __global__ void __launch_bounds__(kStepThreads) k_init(StepArgs a) {
@@ -272,9 +301,9 @@ __global__ void k_tick(long long* interval) { *interval += 1; }
 
 constexpr size_t kMaxStageSmem = 3 * sizeof(float) * kMaxNodes;
 
-size_t stage_smem_bytes(const StepArgs& a) { return 3 * sizeof(float) * (size_t)a.n_pad; }
-
 }  // namespace
+
+size_t stage_smem_bytes(const StepArgs& a) { return 3 * sizeof(float) * (size_t)a.n_pad; }
 
 int configure_step_kernels() {
     int smem = (int)kMaxStageSmem;
@@ -285,6 +314,28 @@ int configure_step_kernels() {
     BPM_CK(cudaFuncSetAttribute(k_stage2<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage2<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage1_groups<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage1_groups<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage1_groups<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage2_groups<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage2_groups<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_stage2_groups<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return BPM_OK;
+}
+
+int stage_blocks_per_sm(int threads, size_t smem, int* blocks) {
+    int b1 = 0, b2 = 0;
+    if (threads == 128) {
+        BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_stage1_groups<128>, 128, smem));
+        BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_stage2_groups<128>, 128, smem));
+    } else if (threads == 512) {
+        BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_stage1_groups<512>, 512, smem));
+        BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_stage2_groups<512>, 512, smem));
+    } else {
+        BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_stage1_groups<256>, 256, smem));
+        BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_stage2_groups<256>, 256, smem));
+    }
+    *blocks = std::min(b1, b2);
     return BPM_OK;
 }
 
@@ -305,6 +356,24 @@ void launch_stage2(const StepArgs& a, int j, cudaStream_t s) {
         k_stage2<512><<<a.B, 512, sm, s>>>(a, j);
     else
         k_stage2<256><<<a.B, 256, sm, s>>>(a, j);
+}
+void launch_stage1_groups(const StageGroups& G, int threads, size_t smem, int j, cudaStream_t s) {
+    const int blocks = G.block_begin[G.ng];
+    if (threads == 128)
+        k_stage1_groups<128><<<blocks, 128, smem, s>>>(G, j);
+    else if (threads == 512)
+        k_stage1_groups<512><<<blocks, 512, smem, s>>>(G, j);
+    else
+        k_stage1_groups<256><<<blocks, 256, smem, s>>>(G, j);
+}
+void launch_stage2_groups(const StageGroups& G, int threads, size_t smem, int j, cudaStream_t s) {
+    const int blocks = G.block_begin[G.ng];
+    if (threads == 128)
+        k_stage2_groups<128><<<blocks, 128, smem, s>>>(G, j);
+    else if (threads == 512)
+        k_stage2_groups<512><<<blocks, 512, smem, s>>>(G, j);
+    else
+        k_stage2_groups<256><<<blocks, 256, smem, s>>>(G, j);
 }
 void launch_init(const StepArgs& a, cudaStream_t s) { k_init<<<a.B, kStepThreads, 0, s>>>(a); }
 void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaStream_t s) {

@@ -39,8 +39,25 @@ struct StepArgs {
 
 constexpr int kStepThreads = 256;
 
+// one stage launch over several mesh groups of a batch: CTAs
+// [block_begin[g], block_begin[g + 1]) integrate the islands of group g.  Passed
+// by value (a grid-constant kernel parameter, under 10 KB); the groups of one
+// launch share the CTA size, and the dynamic shared memory is the largest
+// group's.
+constexpr int kMaxStageGroups = 32;
+struct StageGroups {
+    int ng;
+    int block_begin[kMaxStageGroups + 1];
+    StepArgs a[kMaxStageGroups];
+};
+
 void launch_stage1(const StepArgs& a, int j, cudaStream_t s);
 void launch_stage2(const StepArgs& a, int j, cudaStream_t s);
+void launch_stage1_groups(const StageGroups& G, int threads, size_t smem, int j, cudaStream_t s);
+void launch_stage2_groups(const StageGroups& G, int threads, size_t smem, int j, cudaStream_t s);
+size_t stage_smem_bytes(const StepArgs& a);
+// resident CTAs per SM of the grouped stage kernels at this CTA size and shared memory
+int stage_blocks_per_sm(int threads, size_t smem, int* blocks);
 void launch_init(const StepArgs& a, cudaStream_t s);
 void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaStream_t s);
 void launch_interval_tick(long long* interval, cudaStream_t s);

@@ -36,14 +36,17 @@ def _state(xyz, B, seed):
     return (m / np.linalg.norm(m, axis=1, keepdims=True)).astype(np.float32)
 
 
-def _demag(ctx, isl, p, prec, m):
+def _demag(ctx, isl, p, prec, m, tile_n=None):
     with ctx.batch(isl, p, precision=prec) as bt:
+        if tile_n is not None:
+            bt.set_tuning(tile_n, 256)
         bt.set_state(m, 0.0)
         return bt.field(0.0, L.TERM_DEMAG)
 
 
+@pytest.mark.parametrize("tile_n", [256, 128])
 @pytest.mark.parametrize("case", ["ragged_small", "census"])
-def test_tc_gemm_matches_split_reference_and_fp32(ctx, case):
+def test_tc_gemm_matches_split_reference_and_fp32(ctx, case, tile_n):
     if case == "ragged_small":
         mesh = synth.layered_island_mesh(8.0, 7.0, 3.0, rings=2, hard_slabs=10, soft_slabs=5, seed=4)
         B = 200                           # two 128-row tiles, second one partly padding
@@ -59,16 +62,50 @@ def test_tc_gemm_matches_split_reference_and_fp32(ctx, case):
     m = _state(mesh.xyz_nm, B, 5)
     f32 = _demag(ctx, isl, p, L.PREC_FP32, m)
     ref = _demag(ctx, isl, p, L.PREC_BF16X3_REF, m)
-    tc3 = _demag(ctx, isl, p, L.PREC_BF16X3, m)
-    tc1 = _demag(ctx, isl, p, L.PREC_BF16, m)
+    tc3 = _demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n)
+    tc1 = _demag(ctx, isl, p, L.PREC_BF16, m, tile_n)
     scale = np.abs(f32).max()
     K = 3 * info["n_pad"]
     acc_bound = (3 * K / 16) * 2.0 ** -23
     e_ref = np.abs(tc3 - ref).max() / scale
     e_f32 = np.abs(tc3 - f32).max() / scale
     e_1 = np.abs(tc1 - f32).max() / scale
-    print(f"{case}: |tc3-ref| {e_ref:.2e}  |tc3-f32| {e_f32:.2e}  |tc1-f32| {e_1:.2e}  scale {scale:.3f} T")
+    print(f"{case} TN={tile_n}: |tc3-ref| {e_ref:.2e}  |tc3-f32| {e_f32:.2e}  |tc1-f32| {e_1:.2e}  scale {scale:.3f} T")
     assert np.all(np.isfinite(tc3)) and np.all(np.isfinite(tc1))
     assert e_ref <= acc_bound
     assert e_f32 <= acc_bound + 4 * 2.0 ** -17
     assert e_1 <= 2e-2
+
+
+def test_grouped_gemm_over_mesh_groups(ctx):
+    # one persistent launch covers the tiles of three mesh groups of different
+    # K (and a group smaller than one 128-row tile); every group must meet the
+    # single-group bound against its own FP32 product
+    meshes = [synth.small_island_mesh(seed=0),
+              synth.layered_island_mesh(8.0, 7.0, 3.0, rings=2, hard_slabs=10, soft_slabs=5, seed=4),
+              synth.layered_island_mesh(9.0, 7.0, 3.0, rings=2, hard_slabs=8, soft_slabs=3, aspect=1.5, seed=6)]
+    mids = [ctx.mesh_upload(msh, synth.ecc_materials()) for msh in meshes]
+    sizes = [300, 40, 170]
+    isl = synth.Islands.concat([synth.jittered_islands(b, seed=9 + k, mesh_id=mids[k])
+                                for k, b in enumerate(sizes)])
+    p = synth.RunParams(dt_ps=0.1, substeps=1, term_mask=L.TERM_DEMAG)
+    nmax = max(msh.n_nodes for msh in meshes)
+    rng = np.random.default_rng(7)
+    m = rng.standard_normal((len(isl), 3, nmax)) * 0.3
+    m[:, 2, :] += 1.0
+    m = (m / np.linalg.norm(m, axis=1, keepdims=True)).astype(np.float32)
+    for k, msh in enumerate(meshes):          # nodes past a mesh's own count are not read
+        rows = np.where(isl.mesh_id == mids[k])[0]
+        m[np.ix_(rows, [0, 1, 2], np.arange(msh.n_nodes, nmax))] = 0.0
+    f32 = _demag(ctx, isl, p, L.PREC_FP32, m)
+    for tile_n in (256, 128):
+        tc3 = _demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n)
+        assert np.all(np.isfinite(tc3))
+        for k, msh in enumerate(meshes):
+            rows = np.where(isl.mesh_id == mids[k])[0]
+            n = msh.n_nodes
+            K = 3 * ctx.mesh_info(mids[k])["n_pad"]
+            scale = np.abs(f32[rows][:, :, :n]).max()
+            err = np.abs(tc3[rows][:, :, :n] - f32[rows][:, :, :n]).max() / scale
+            print(f"group {k} (B={sizes[k]}, K={K}) TN={tile_n}: |tc3-f32| {err:.2e}")
+            assert err <= (3 * K / 16) * 2.0 ** -23 + 4 * 2.0 ** -17
