@@ -104,6 +104,32 @@ def peaks():
         return None
 
 
+def gemm_peak(pk):
+    """Denominator of the GEMM roofline.  The GEMM duration is taken launch by
+    launch with CUDA events (bpm_batch_kernel_times, right after the timed
+    region, same stream and launch configuration), a kernel timed alone at the
+    clocks of the run (2.0-2.07 GHz), so the burst cuBLAS figure applies; the
+    sustained one was taken over seconds of back-to-back GEMMs at a median SM
+    clock of 1455 MHz."""
+    if pk:
+        return pk["bf16_tflops"], "MEASURED_PEAKS bf16_tflops (burst; kernel timed launch by launch)"
+    return 1900.0, "fallback (1.9 PFLOP/s bf16 burst)"
+
+
+# DRAM bytes (read + write) of one demag-GEMM launch from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), keyed by
+# (precision, islands, nodes) of the captured workload:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
+#       --clock-control none -k regex:k_gemm_grouped -s 10 -c 2 --csv \
+#       python bench.py --steps 2 --warmup 1 --no-cpu --no-e2e --no-extras --no-autotune
+# (k_gemm_grouped<3,256>, M-major tile order).  Remove an entry when the kernel changes.
+NCU_GEMM_TRAFFIC = {(1, 4096, 1547): 445.91e6 + 60.33e6}
+
+
+def gemm_traffic(prec, B, n):
+    return NCU_GEMM_TRAFFIC.get((int(prec), int(B), int(n)))
+
+
 def run_oracle_sample(islands, n_intervals, k, mesh, mats, hm, p):
     """Time the FP64 oracle on a bounded sample; returns seconds."""
     from oracle import fem, llg
@@ -251,11 +277,12 @@ def main_uneven(args):
     clocks = sample_clocks_stop(proc, cf, 0)
     ms = e0.elapsed_time(e1)
     ok = bool(np.all(bt.read()["status"] == 0))
+    launches_per_interval = bt.graph_kernels()
     kt = bt.kernel_times(reps=4)
     flops = sum(6.0 * int(np.sum(isl.mesh_id == mid)) * (3 * v["mesh"].n_nodes) ** 2
                 for mid, v in zip(mids, variants))
     pk = peaks()
-    peak = pk["bf16_tflops_sustained"] if pk else 1700.0
+    peak, peak_source = gemm_peak(pk)
     B = len(isl)
     line = {"metric": METRIC, "value": B * args.steps * DT_PS * 1e-3 / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -265,10 +292,11 @@ def main_uneven(args):
                                    f"{max(v['mesh'].n_nodes for v in variants)} nodes), {args.realisations} "
                                    "jittered targets + 2 staggered adjacent-track islands each",
                        "islands": B, "heun_steps_per_interval": p.substeps, "dt_ps": DT_PS},
-            "gpu_launches": args.steps * (4 * p.substeps * len(variants) + 1),
+            "gpu_launches": args.steps * launches_per_interval,
             "roofline": {"bound": "tensor", "achieved": flops / (kt["gemm_ms"] * 1e-3) / 1e12, "peak": peak,
-                         "unit": "TFLOP/s", "frac": flops / (kt["gemm_ms"] * 1e-3) / 1e12 / peak, "traffic": None,
-                         "kernel": "demag GEMMs of all 16 groups (summed)"},
+                         "unit": "TFLOP/s", "peak_source": peak_source,
+                         "frac": flops / (kt["gemm_ms"] * 1e-3) / 1e12 / peak, "traffic": None,
+                         "kernel": "grouped demag GEMM over the 16 mesh groups (one launch)"},
             "kernel_ms": kt, "clocks": clocks, "status_ok": ok}
     bt.destroy()
     ctx.close()
@@ -340,6 +368,7 @@ def main(args):
     ok = bool(np.all(out["status"] == 0))
     value = world * B * args.steps * DT_PS * 1e-3 / (ms * 1e-3)
     # kernel durations (events on the launching stream, outside the graph)
+    launches_per_interval = bt.graph_kernels()
     kt = bt.kernel_times(reps=max(4, min(2 * k, 40)))
     bt.destroy()
     n = mesh.n_nodes
@@ -352,11 +381,11 @@ def main(args):
                 "peak": SM_FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"}
     else:
-        peak = pk["bf16_tflops_sustained"] if pk else 1700.0
+        peak, peak_source = gemm_peak(pk)
         roof = {"bound": "tensor", "achieved": gemm_flops / (kt["gemm_ms"] * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained" if pk else "fallback"}
+                "unit": "TFLOP/s", "peak_source": peak_source}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = gemm_traffic(prec, B, n)
     roof["kernel"] = "demag GEMM"
     # step kernels: algorithmic HBM bytes (stage 1: 60 n, stage 2: 72 n per island)
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
@@ -404,7 +433,7 @@ def main(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"bf16x3": "bf16x3+f32", "fp32": "f32", "bf16": "bf16+f32"}[args.precision],
             "data": "synthetic", "config": config_dict(mesh, k, args.precision, B, world),
-            "e2e": e2e, "gpu_launches": args.steps * (4 * k + 1), "roofline": roof, "roofline_step_kernels": roof_steps,
+            "e2e": e2e, "gpu_launches": args.steps * launches_per_interval, "roofline": roof, "roofline_step_kernels": roof_steps,
             "kernel_ms": kt, "tuning": tuning, "clocks": clocks, "status_ok": ok, **extras}
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(mesh, mats, hm, p, k)

@@ -209,17 +209,29 @@ int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out
  * clock does not; call bpm_batch_set_state afterwards to restart a run. */
 int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double* stage1_ms,
                            double* stage2_ms);
+/* Order in which the persistent tensor-core GEMM walks a group's output tiles.
+ * M-major: consecutive tiles share rows of the batch operand (the demag
+ * operator is swept once per wave of CTAs); N-major: consecutive tiles share
+ * rows of the operator (the batch operand is swept once per wave).  AUTO takes
+ * N-major for a group whose operator does not fit in L2 and has more rows
+ * than the batch, so that it is read from HBM once and the batch operand is
+ * re-read from L2; M-major otherwise. */
+enum { BPM_RASTER_AUTO = 0, BPM_RASTER_M = 1, BPM_RASTER_N = 2 };
+
 /* Launch configuration of a batch's kernels. */
 typedef struct {
     int32_t gemm_tile_n;     /* output columns per demag-GEMM CTA: 256 or 128 */
     int32_t stage_threads;   /* threads per Heun-stage CTA: 128, 256 or 512 */
+    int32_t gemm_raster;     /* BPM_RASTER_*: tile order of the tensor-core GEMM */
+    int32_t reserved;        /* 0 */
     double  gemm_ms;         /* measured time of one demag GEMM over the batch (autotune output) */
     double  stage_ms;        /* measured time of one predictor + one corrector over the batch */
 } bpm_tuning;
 
-/* Autotuner: time every (gemm_tile_n, stage_threads) candidate on this batch
- * with CUDA events (reps Heun steps each, kernel by kernel), apply the fastest
- * GEMM tile and stage CTA size, and report them in *chosen (nullable).  The
+/* Autotuner: time every (gemm_tile_n, gemm_raster) candidate of the demag GEMM
+ * and every stage_threads candidate on this batch with CUDA events (reps Heun
+ * steps each, kernel by kernel), apply the fastest of each, and report them in
+ * *chosen (nullable).  The
  * state advances by the timed steps but the batch clock does not; call
  * bpm_batch_set_state afterwards to restart a run.  Tile shapes are an
  * implementation choice of this library, not of the paper. */
@@ -231,6 +243,9 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t);
  * launches of the batch then return at once, and bpm_batch_read reports
  * BPM_ERR_TIMEOUT.  code = 0 clears the flag. */
 int bpm_debug_set_gemm_error(bpm_batch* bt, int32_t code);
+/* Number of kernel launches in the batch's one-interval CUDA graph (the
+ * graph exists after the first bpm_batch_advance; BPM_ERR_STATE before). */
+int bpm_batch_graph_kernels(bpm_batch* bt, int32_t* n_kernels);
 /* Current simulated time of the batch. */
 int bpm_batch_time(bpm_batch* bt, double* t_ps);
 int bpm_batch_destroy(bpm_batch* bt);

@@ -56,8 +56,12 @@ class bpm_train_cfg(ctypes.Structure):
                 ("beta1", c_float), ("beta2", c_float), ("eps", c_float), ("pad_", c_int32)]
 
 
+RASTER_AUTO, RASTER_M, RASTER_N = 0, 1, 2
+
+
 class bpm_tuning(ctypes.Structure):
-    _fields_ = [("gemm_tile_n", c_int32), ("stage_threads", c_int32), ("gemm_ms", c_double), ("stage_ms", c_double)]
+    _fields_ = [("gemm_tile_n", c_int32), ("stage_threads", c_int32), ("gemm_raster", c_int32), ("reserved", c_int32),
+                ("gemm_ms", c_double), ("stage_ms", c_double)]
 
 
 # name -> (restype, argtypes); every function declared in include/bpm.h
@@ -82,6 +86,7 @@ PROTOTYPES = {
     "bpm_batch_autotune": (c_int, [c_void_p, c_int32, POINTER(bpm_tuning)]),
     "bpm_batch_set_tuning": (c_int, [c_void_p, POINTER(bpm_tuning)]),
     "bpm_debug_set_gemm_error": (c_int, [c_void_p, c_int32]),
+    "bpm_batch_graph_kernels": (c_int, [c_void_p, POINTER(c_int32)]),
     "bpm_batch_time": (c_int, [c_void_p, POINTER(c_double)]),
     "bpm_batch_destroy": (c_int, [c_void_p]),
     "bpm_run_batch": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,

@@ -275,14 +275,20 @@ class Batch:
         L.check(self.lib.bpm_batch_kernel_times(self.h, int(reps), byref(g), byref(s1), byref(s2)))
         return dict(gemm_ms=g.value, stage1_ms=s1.value, stage2_ms=s2.value)
 
+    def graph_kernels(self) -> int:
+        """Kernel launches per interval in the batch's CUDA graph."""
+        n = c_int32()
+        L.check(self.lib.bpm_batch_graph_kernels(self.h, byref(n)))
+        return n.value
+
     def autotune(self, reps: int = 4) -> dict:
         t = L.bpm_tuning()
         L.check(self.lib.bpm_batch_autotune(self.h, int(reps), byref(t)))
-        return dict(gemm_tile_n=t.gemm_tile_n, stage_threads=t.stage_threads, gemm_ms=t.gemm_ms,
-                    stage_ms=t.stage_ms)
+        return dict(gemm_tile_n=t.gemm_tile_n, stage_threads=t.stage_threads, gemm_raster=t.gemm_raster,
+                    gemm_ms=t.gemm_ms, stage_ms=t.stage_ms)
 
-    def set_tuning(self, gemm_tile_n: int, stage_threads: int, **_):
-        t = L.bpm_tuning(int(gemm_tile_n), int(stage_threads), 0.0, 0.0)
+    def set_tuning(self, gemm_tile_n: int, stage_threads: int, gemm_raster: int = L.RASTER_AUTO, **_):
+        t = L.bpm_tuning(int(gemm_tile_n), int(stage_threads), int(gemm_raster), 0, 0.0, 0.0)
         L.check(self.lib.bpm_batch_set_tuning(self.h, byref(t)))
 
     def tuning_key(self, device_name: str = "") -> str:

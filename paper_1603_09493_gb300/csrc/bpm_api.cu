@@ -52,6 +52,7 @@ struct bpm_batch {
     std::vector<cudaStream_t> side;   // fork streams for the groups of a multi-mesh batch
     std::vector<cudaEvent_t> ev;
     int tile_n = 256;                 // demag GEMM output columns per CTA
+    int raster = BPM_RASTER_AUTO;     // demag GEMM tile order
     GroupedGemm gg;                   // tensor-core demag GEMM over all groups (BF16 precisions)
 };
 
@@ -89,7 +90,8 @@ int setup_grouped_gemm(bpm_batch* bt) {
         const int K = g.mesh->K();
         ops.push_back(GemmOperands{g.Ahi, g.Alo, g.mesh->Nhi, g.mesh->Nlo, g.Hd, g.Bp, K, K});
     }
-    return grouped_gemm_setup(&bt->gg, ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1);
+    return grouped_gemm_setup(&bt->gg, ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1, bt->raster,
+                              bt->ctx->l2_bytes);
 }
 
 // demag GEMM of every group's current operand A -> Hd: one persistent launch
@@ -288,6 +290,7 @@ int bpm_create(bpm_ctx** out, int device, void* cuda_stream) {
     bpm_ctx* c = new bpm_ctx();
     c->device = device;
     c->sm_count = prop.multiProcessorCount;
+    c->l2_bytes = (size_t)prop.l2CacheSize;
     if (cuda_stream) {
         c->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -725,6 +728,29 @@ int bpm_batch_advance(bpm_batch* bt, int32_t n_intervals) {
     return BPM_OK;
 }
 
+int bpm_batch_graph_kernels(bpm_batch* bt, int32_t* n_kernels) {
+    if (!bt || !n_kernels) {
+        set_error("null argument");
+        return BPM_ERR_ARG;
+    }
+    if (!bt->graph) {
+        set_error("no interval graph yet: advance the batch first");
+        return BPM_ERR_STATE;
+    }
+    size_t n = 0;
+    BPM_CK(cudaGraphGetNodes(bt->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    BPM_CK(cudaGraphGetNodes(bt->graph, nodes.data(), &n));
+    int k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        BPM_CK(cudaGraphNodeGetType(nd, &t));
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *n_kernels = k;
+    return BPM_OK;
+}
+
 int bpm_batch_read(bpm_batch* bt, float* m, int32_t ld, uint8_t* switched, float* t_sw_ps, int32_t* status, float* mz,
                    int on_device) {
     if (!bt) {
@@ -886,13 +912,15 @@ int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double*
 
 int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
     if (!bt || !t || (t->gemm_tile_n != 128 && t->gemm_tile_n != 256) ||
-        (t->stage_threads != 128 && t->stage_threads != 256 && t->stage_threads != 512)) {
-        set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512)");
+        (t->stage_threads != 128 && t->stage_threads != 256 && t->stage_threads != 512) ||
+        (t->gemm_raster != BPM_RASTER_AUTO && t->gemm_raster != BPM_RASTER_M && t->gemm_raster != BPM_RASTER_N)) {
+        set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512, gemm_raster 0|1|2)");
         return BPM_ERR_ARG;
     }
     BPM_TRY(ensure_device(bt->ctx));
     BPM_CK(cudaStreamSynchronize(bt->ctx->stream));
     bt->tile_n = t->gemm_tile_n;
+    bt->raster = t->gemm_raster;
     for (auto& g : bt->groups) g.args.threads = t->stage_threads;
     drop_graph(bt);   // the graph holds the old launch configurations
     if (tensor_core_precision(bt)) BPM_TRY(setup_grouped_gemm(bt));
@@ -905,27 +933,37 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
         return BPM_ERR_ARG;
     }
     const int tiles[2] = {256, 128};
+    const int rasters[3] = {BPM_RASTER_AUTO, BPM_RASTER_M, BPM_RASTER_N};
     const int threads[3] = {256, 128, 512};
-    const bool tc = bt->p.precision == BPM_PREC_BF16X3 || bt->p.precision == BPM_PREC_BF16;
+    const bool tc = tensor_core_precision(bt);
     double best_g = 1e300, best_s = 1e300;
-    int bt_n = 256, bt_t = 256;
+    int bt_n = 256, bt_r = BPM_RASTER_AUTO, bt_t = 256;
+    // the GEMM candidates at the default stage CTA size, then the stage CTA sizes at the best GEMM
     for (int ti = 0; ti < (tc ? 2 : 1); ++ti)
-        for (int hi = 0; hi < 3; ++hi) {
-            bpm_tuning t{tiles[ti], threads[hi], 0, 0};
+        for (int ri = 0; ri < (tc ? 3 : 1); ++ri) {
+            bpm_tuning t{tiles[ti], 256, rasters[ri], 0, 0, 0};
             BPM_TRY(bpm_batch_set_tuning(bt, &t));
             double g = 0, s1 = 0, s2 = 0;
             BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));   // warm-up
             BPM_TRY(bpm_batch_kernel_times(bt, reps, &g, &s1, &s2));
-            if (hi == 0 && g < best_g) {
+            if (g < best_g) {
                 best_g = g;
                 bt_n = tiles[ti];
-            }
-            if (ti == 0 && s1 + s2 < best_s) {
-                best_s = s1 + s2;
-                bt_t = threads[hi];
+                bt_r = rasters[ri];
             }
         }
-    bpm_tuning t{bt_n, bt_t, best_g, best_s};
+    for (int hi = 0; hi < 3; ++hi) {
+        bpm_tuning t{bt_n, threads[hi], bt_r, 0, 0, 0};
+        BPM_TRY(bpm_batch_set_tuning(bt, &t));
+        double g = 0, s1 = 0, s2 = 0;
+        BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));
+        BPM_TRY(bpm_batch_kernel_times(bt, reps, &g, &s1, &s2));
+        if (s1 + s2 < best_s) {
+            best_s = s1 + s2;
+            bt_t = threads[hi];
+        }
+    }
+    bpm_tuning t{bt_n, bt_t, bt_r, 0, best_g, best_s};
     BPM_TRY(bpm_batch_set_tuning(bt, &t));
     if (chosen) *chosen = t;
     return BPM_OK;

@@ -4,7 +4,9 @@
 //   C_g[M_g][N_g] = sum of the BF16 split products of A_g[M_g][K_g] and W_g[N_g][K_g]^T
 // (3 products hi*hi + lo*hi + hi*lo, or 1), FP32 accumulate in TMEM.  The
 // 128 x TN output tiles of all groups form one list; each CTA (one per SM)
-// walks it with a stride of the grid size.  Warp roles:
+// walks it with a stride of the grid size.  Within a group the tiles run
+// M-major or N-major (chosen per group), so that a wave of CTAs shares the
+// larger operand's rows in L2 and it is read from HBM once.  Warp roles:
 //   warp 0  one lane streams the k-blocks of every tile with TMA into a ring of
 //           shared-memory stages (the ring runs across tile boundaries);
 //   warp 1  allocates two TMEM accumulators; one lane issues the MMAs, tile i
@@ -38,6 +40,15 @@ __device__ __forceinline__ int find_group(const GemmGroupDev* __restrict__ G, in
     int g = 0;
     while (g + 1 < ng && t >= G[g + 1].tile_begin) ++g;
     return g;
+}
+
+// output tile lt of group gg -> first row (M) and column (N)
+template <int TN>
+__device__ __forceinline__ void tile_origin(const GemmGroupDev& gg, int lt, int& m0, int& n0) {
+    const int mt = gg.n_major ? lt % gg.tiles_m : lt / gg.tiles_n;
+    const int nt = gg.n_major ? lt / gg.tiles_m : lt % gg.tiles_n;
+    m0 = mt * TM;
+    n0 = nt * TN;
 }
 
 template <int P, int TN>
@@ -99,8 +110,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
         for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
             const int g = find_group(G, ng, t);
             const GemmGroupDev& gg = G[g];
-            const int lt = t - gg.tile_begin;
-            const int m0 = (lt / gg.tiles_n) * TM, n0 = (lt % gg.tiles_n) * TN;
+            int m0, n0;
+            tile_origin<TN>(gg, t - gg.tile_begin, m0, n0);
             const int nk = gg.K / TK;
             for (int kb = 0; kb < nk; ++kb, ++kbg) {
                 const int s = kbg % S;
@@ -159,8 +170,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
         for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++i) {
             const int g = find_group(G, ng, t);
             const GemmGroupDev& gg = G[g];
-            const int lt = t - gg.tile_begin;
-            const int m0 = (lt / gg.tiles_n) * TM, n0 = (lt % gg.tiles_n) * TN;
+            int m0, n0;
+            tile_origin<TN>(gg, t - gg.tile_begin, m0, n0);
             const int a = i & 1;
             const bool have = mbar_wait(accf_bar(a), (i >> 1) & 1, err, 15);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -214,9 +225,14 @@ int launch_grouped(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err
 
 }  // namespace
 
-int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products) {
+int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products, int raster,
+                       size_t l2_bytes) {
     if (tile_n != 128 && tile_n != 256) {
         set_error("grouped GEMM tile width must be 128 or 256");
+        return BPM_ERR_ARG;
+    }
+    if (raster != BPM_RASTER_AUTO && raster != BPM_RASTER_M && raster != BPM_RASTER_N) {
+        set_error("unknown GEMM raster %d", raster);
         return BPM_ERR_ARG;
     }
     std::vector<GemmGroupDev> h(ops.size());
@@ -243,9 +259,15 @@ int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, in
         h[g].N = o.N;
         h[g].K = o.K;
         h[g].ldc = o.N;
+        h[g].tiles_m = o.M / tc::TM;
         h[g].tiles_n = (o.N + tile_n - 1) / tile_n;
         h[g].tile_begin = tiles;
-        tiles += (o.M / tc::TM) * h[g].tiles_n;
+        // AUTO: N-major when the operator (N x K, every split part) does not fit in L2 and
+        // has more rows than the batch operand
+        const size_t w_bytes = (size_t)o.N * o.K * sizeof(__nv_bfloat16) * (products == 3 ? 2 : 1);
+        const bool auto_n = w_bytes > l2_bytes && o.N > o.M;
+        h[g].n_major = raster == BPM_RASTER_N || (raster == BPM_RASTER_AUTO && auto_n) ? 1 : 0;
+        tiles += h[g].tiles_m * h[g].tiles_n;
     }
     grouped_gemm_free(gg);
     BPM_CK(cudaMalloc(&gg->d_groups, h.size() * sizeof(GemmGroupDev)));

@@ -79,6 +79,7 @@ void free_mlp(Mlp* m);
 struct bpm_ctx {
     int device = 0;
     int sm_count = 0;
+    size_t l2_bytes = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<bpm::Mesh*> meshes;
@@ -120,7 +121,9 @@ struct GemmGroupDev {   // CUtensorMap members carry the 64-byte alignment TMA n
     CUtensorMap ahi, alo, whi, wlo;   // 128 B each, 64-byte aligned
     float* C;
     int M, N, K, ldc;
-    int tiles_n, tile_begin;          // N tiles of this group; first tile in the global list
+    int tiles_m, tiles_n;             // output tiles of this group along M and N
+    int tile_begin;                   // first tile of this group in the launch's list
+    int n_major;                      // tile order: 1 = consecutive tiles share the W rows
 };
 struct GemmOperands {
     const __nv_bfloat16 *Ahi, *Alo, *Whi, *Wlo;
@@ -131,7 +134,8 @@ struct GroupedGemm {
     GemmGroupDev* d_groups = nullptr;
     int n_groups = 0, total_tiles = 0, tile_n = 256, products = 3;
 };
-int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products);
+int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products, int raster,
+                       size_t l2_bytes);
 void grouped_gemm_free(GroupedGemm* gg);
 int grouped_gemm_launch(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err);
 int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows);

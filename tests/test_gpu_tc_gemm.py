@@ -36,10 +36,10 @@ def _state(xyz, B, seed):
     return (m / np.linalg.norm(m, axis=1, keepdims=True)).astype(np.float32)
 
 
-def _demag(ctx, isl, p, prec, m, tile_n=None):
+def _demag(ctx, isl, p, prec, m, tile_n=None, raster=L.RASTER_AUTO):
     with ctx.batch(isl, p, precision=prec) as bt:
         if tile_n is not None:
-            bt.set_tuning(tile_n, 256)
+            bt.set_tuning(tile_n, 256, raster)
         bt.set_state(m, 0.0)
         return bt.field(0.0, L.TERM_DEMAG)
 
@@ -101,6 +101,9 @@ def test_grouped_gemm_over_mesh_groups(ctx):
     for tile_n in (256, 128):
         tc3 = _demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n)
         assert np.all(np.isfinite(tc3))
+        # the tile order changes which CTA computes a tile, never its summation
+        for raster in (L.RASTER_M, L.RASTER_N):
+            assert np.array_equal(_demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n, raster), tc3)
         for k, msh in enumerate(meshes):
             rows = np.where(isl.mesh_id == mids[k])[0]
             n = msh.n_nodes
