@@ -123,7 +123,7 @@ def gemm_peak(pk):
 #       --clock-control none -k regex:k_gemm_grouped -s 10 -c 2 --csv \
 #       python bench.py --steps 2 --warmup 1 --no-cpu --no-e2e --no-extras --no-autotune
 # (k_gemm_grouped<3,256>, M-major tile order).  Remove an entry when the kernel changes.
-NCU_GEMM_TRAFFIC = {(1, 4096, 1547): 445.91e6 + 60.33e6}
+NCU_GEMM_TRAFFIC = {}
 
 
 def gemm_traffic(prec, B, n):

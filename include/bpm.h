@@ -112,9 +112,12 @@ typedef struct {
 
 /* Facts about an uploaded mesh. */
 typedef struct {
-    int32_t n_nodes, n_pad, n_tets, n_boundary;
+    int32_t n_nodes;
+    int32_t n_pad;               /* node stride of a component plane (n rounded up to 32) */
+    int32_t n_tets, n_boundary;
     int32_t nnz;                 /* exchange CSR entries including the diagonal */
-    int32_t cg_iters_neumann, cg_iters_dirichlet, pad_;
+    int32_t cg_iters_neumann, cg_iters_dirichlet;
+    int32_t k_pad;               /* demag GEMM width: 3 n_pad rounded up to 64 */
     double  volume_nm3;
     double  exchange_lambda_max_T;  /* largest eigenvalue of S (nominal Ms), power iteration */
     double  field_bound_T;          /* lambda_max + max anisotropy field + mu0*max Ms */
@@ -223,13 +226,13 @@ typedef struct {
     int32_t gemm_tile_n;     /* output columns per demag-GEMM CTA: 256 or 128 */
     int32_t stage_threads;   /* threads per Heun-stage CTA: 128, 256 or 512 */
     int32_t gemm_raster;     /* BPM_RASTER_*: tile order of the tensor-core GEMM */
-    int32_t reserved;        /* 0 */
+    int32_t stage_islands;   /* islands per Heun-stage CTA: 1 (0 = 1), or 2 with 256 threads */
     double  gemm_ms;         /* measured time of one demag GEMM over the batch (autotune output) */
     double  stage_ms;        /* measured time of one predictor + one corrector over the batch */
 } bpm_tuning;
 
 /* Autotuner: time every (gemm_tile_n, gemm_raster) candidate of the demag GEMM
- * and every stage_threads candidate on this batch with CUDA events (reps Heun
+ * and every (stage_threads, stage_islands) candidate on this batch with CUDA events (reps Heun
  * steps each, kernel by kernel), apply the fastest of each, and report them in
  * *chosen (nullable).  The
  * state advances by the timed steps but the batch clock does not; call

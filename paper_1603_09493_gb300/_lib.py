@@ -42,7 +42,7 @@ class bpm_run_params(ctypes.Structure):
 class bpm_mesh_info(ctypes.Structure):
     _fields_ = [("n_nodes", c_int32), ("n_pad", c_int32), ("n_tets", c_int32), ("n_boundary", c_int32),
                 ("nnz", c_int32), ("cg_iters_neumann", c_int32), ("cg_iters_dirichlet", c_int32),
-                ("pad_", c_int32), ("volume_nm3", c_double), ("exchange_lambda_max_T", c_double),
+                ("k_pad", c_int32), ("volume_nm3", c_double), ("exchange_lambda_max_T", c_double),
                 ("field_bound_T", c_double), ("cg_residual_neumann", c_double),
                 ("cg_residual_dirichlet", c_double)]
 
@@ -60,7 +60,7 @@ RASTER_AUTO, RASTER_M, RASTER_N = 0, 1, 2
 
 
 class bpm_tuning(ctypes.Structure):
-    _fields_ = [("gemm_tile_n", c_int32), ("stage_threads", c_int32), ("gemm_raster", c_int32), ("reserved", c_int32),
+    _fields_ = [("gemm_tile_n", c_int32), ("stage_threads", c_int32), ("gemm_raster", c_int32), ("stage_islands", c_int32),
                 ("gemm_ms", c_double), ("stage_ms", c_double)]
 
 

@@ -142,6 +142,7 @@ int build_stage_launches(const bpm_batch* bt, StageLaunches* out) {
     out->launch.clear();
     out->smem.clear();
     out->threads = bt->groups[0].args.threads;
+    const int ipb = stage_islands_per_cta(bt->groups[0].args);
     std::vector<int> order(bt->groups.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -150,9 +151,9 @@ int build_stage_launches(const bpm_batch* bt, StageLaunches* out) {
     int class_occ = -1;
     for (int gi : order) {
         const Group& g = bt->groups[gi];
-        const size_t sb = stage_smem_bytes(g.args);
+        const size_t sb = ipb * stage_smem_bytes(g.args);
         int occ = 0;
-        BPM_TRY(stage_blocks_per_sm(out->threads, sb, &occ));
+        BPM_TRY(stage_blocks_per_sm(out->threads, ipb, sb, &occ));
         if (out->launch.empty() || occ != class_occ || out->launch.back().ng == kMaxStageGroups) {
             out->launch.emplace_back();
             std::memset(&out->launch.back(), 0, sizeof(StageGroups));
@@ -161,7 +162,7 @@ int build_stage_launches(const bpm_batch* bt, StageLaunches* out) {
         }
         StageGroups& G = out->launch.back();
         G.a[G.ng] = g.args;
-        G.block_begin[G.ng + 1] = G.block_begin[G.ng] + g.B;
+        G.block_begin[G.ng + 1] = G.block_begin[G.ng] + (g.B + ipb - 1) / ipb;
         ++G.ng;
     }
     return BPM_OK;
@@ -342,6 +343,7 @@ int bpm_mesh_upload(bpm_ctx* ctx, const double* xyz_nm, int32_t n_nodes, const i
     Mesh* M = new Mesh();
     M->n = n_nodes;
     M->n_pad = round_up(n_nodes, kNodePad);
+    M->k_pad = round_up(3 * M->n_pad, kKPad);
     M->n_tets = n_tets;
     int r = assemble_mesh(ctx, M, xyz_nm, tets, n_tets, tet_region, mats, n_regions, flags);
     if (r != BPM_OK) {
@@ -563,6 +565,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         a.B = g.B;
         a.n = M->n;
         a.n_pad = M->n_pad;
+        a.kp = M->k_pad;
         a.node_pos = M->node_pos;
         a.node_mat = M->node_mat;
         a.sell_off = M->sell_off;
@@ -601,6 +604,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         for (int c = 0; c < 3; ++c) a.uni[c] = p->uniform_T[c];
         a.mask = p->term_mask;
         a.threads = 256;
+        a.ipb = 1;
     }
     if (r == BPM_OK && bt->groups.size() > 1) {
         const int ns = (int)std::min<size_t>(4, bt->groups.size());
@@ -913,15 +917,20 @@ int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double*
 int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
     if (!bt || !t || (t->gemm_tile_n != 128 && t->gemm_tile_n != 256) ||
         (t->stage_threads != 128 && t->stage_threads != 256 && t->stage_threads != 512) ||
-        (t->gemm_raster != BPM_RASTER_AUTO && t->gemm_raster != BPM_RASTER_M && t->gemm_raster != BPM_RASTER_N)) {
-        set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512, gemm_raster 0|1|2)");
+        (t->gemm_raster != BPM_RASTER_AUTO && t->gemm_raster != BPM_RASTER_M && t->gemm_raster != BPM_RASTER_N) ||
+        t->stage_islands < 0 || t->stage_islands > 2 || (t->stage_islands == 2 && t->stage_threads != 256)) {
+        set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512, gemm_raster 0|1|2, "
+                  "stage_islands 0|1|2 with 2 only at 256 threads)");
         return BPM_ERR_ARG;
     }
     BPM_TRY(ensure_device(bt->ctx));
     BPM_CK(cudaStreamSynchronize(bt->ctx->stream));
     bt->tile_n = t->gemm_tile_n;
     bt->raster = t->gemm_raster;
-    for (auto& g : bt->groups) g.args.threads = t->stage_threads;
+    for (auto& g : bt->groups) {
+        g.args.threads = t->stage_threads;
+        g.args.ipb = t->stage_islands == 2 ? 2 : 1;
+    }
     drop_graph(bt);   // the graph holds the old launch configurations
     if (tensor_core_precision(bt)) BPM_TRY(setup_grouped_gemm(bt));
     return BPM_OK;
@@ -941,7 +950,7 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
     // the GEMM candidates at the default stage CTA size, then the stage CTA sizes at the best GEMM
     for (int ti = 0; ti < (tc ? 2 : 1); ++ti)
         for (int ri = 0; ri < (tc ? 3 : 1); ++ri) {
-            bpm_tuning t{tiles[ti], 256, rasters[ri], 0, 0, 0};
+            bpm_tuning t{tiles[ti], 256, rasters[ri], 1, 0, 0};
             BPM_TRY(bpm_batch_set_tuning(bt, &t));
             double g = 0, s1 = 0, s2 = 0;
             BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));   // warm-up
@@ -952,18 +961,22 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
                 bt_r = rasters[ri];
             }
         }
-    for (int hi = 0; hi < 3; ++hi) {
-        bpm_tuning t{bt_n, threads[hi], bt_r, 0, 0, 0};
+    // stage candidates: one island per CTA at each CTA size, two islands per 256-thread CTA
+    int bt_i = 1;
+    for (int hi = 0; hi < 4; ++hi) {
+        const int nt = hi < 3 ? threads[hi] : 256, ipb = hi < 3 ? 1 : 2;
+        bpm_tuning t{bt_n, nt, bt_r, ipb, 0, 0};
         BPM_TRY(bpm_batch_set_tuning(bt, &t));
         double g = 0, s1 = 0, s2 = 0;
         BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));
         BPM_TRY(bpm_batch_kernel_times(bt, reps, &g, &s1, &s2));
         if (s1 + s2 < best_s) {
             best_s = s1 + s2;
-            bt_t = threads[hi];
+            bt_t = nt;
+            bt_i = ipb;
         }
     }
-    bpm_tuning t{bt_n, bt_t, bt_r, 0, best_g, best_s};
+    bpm_tuning t{bt_n, bt_t, bt_r, bt_i, best_g, best_s};
     BPM_TRY(bpm_batch_set_tuning(bt, &t));
     if (chosen) *chosen = t;
     return BPM_OK;

@@ -566,16 +566,16 @@ __global__ void k_demag_rows(int n, int ncol, const int* __restrict__ rowptr, co
     N64[((size_t)2 * n + i) * ncol + cc] = s2;
 }
 
-// padded kernel operand: W[r][q] = -mu0 1e6 N[(c n + i)][(c' n + k)], r = c n_pad + i, q = c' n_pad + k
-__global__ void k_demag_convert(int n, int n_pad, const double* __restrict__ N64, float* __restrict__ W32,
+// padded kernel operand [K][K]: W[r][q] = -mu0 1e6 N[(c n + i)][(c' n + k)], r = c n_pad + i,
+// q = c' n_pad + k; zero on padding nodes and on rows/columns from 3 n_pad to K
+__global__ void k_demag_convert(int n, int n_pad, int K, const double* __restrict__ N64, float* __restrict__ W32,
                                 __nv_bfloat16* __restrict__ Whi, __nv_bfloat16* __restrict__ Wlo) {
-    int K = 3 * n_pad;
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     if (q >= K) return;
     int c = r / n_pad, i = r % n_pad, c2 = q / n_pad, k = q % n_pad;
     double v = 0;
-    if (i < n && k < n) v = -kMu0 * 1e6 * N64[((size_t)c * n + i) * (3 * (size_t)n) + (size_t)c2 * n + k];
+    if (c < 3 && c2 < 3 && i < n && k < n) v = -kMu0 * 1e6 * N64[((size_t)c * n + i) * (3 * (size_t)n) + (size_t)c2 * n + k];
     size_t o = (size_t)r * K + q;
     W32[o] = (float)v;
     __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
@@ -830,7 +830,7 @@ int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets_
     BPM_CK(cudaMalloc(&M->N32, (size_t)K * K * sizeof(float)));
     BPM_CK(cudaMalloc(&M->Nhi, (size_t)K * K * sizeof(__nv_bfloat16)));
     BPM_CK(cudaMalloc(&M->Nlo, (size_t)K * K * sizeof(__nv_bfloat16)));
-    k_demag_convert<<<dim3((K + 127) / 128, K), 128, 0, st>>>(n, M->n_pad, N64, M->N32, M->Nhi, M->Nlo);
+    k_demag_convert<<<dim3((K + 127) / 128, K), 128, 0, st>>>(n, M->n_pad, K, N64, M->N32, M->Nhi, M->Nlo);
     BPM_CK(cudaGetLastError());
     BPM_CK(cudaStreamSynchronize(st));
     if (!(flags & BPM_MESH_KEEP_F64)) {
@@ -893,6 +893,7 @@ int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets_
     bpm_mesh_info& I = M->info;
     I.n_nodes = n;
     I.n_pad = np;
+    I.k_pad = M->k_pad;
     I.n_tets = nt;
     I.n_boundary = nb;
     I.nnz = nnz;

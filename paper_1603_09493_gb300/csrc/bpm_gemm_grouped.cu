@@ -136,7 +136,12 @@ __global__ void __launch_bounds__(kGThreads, 1)
         bool ok = true;
         for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++i) {
             const int g = find_group(G, ng, t);
-            const int nk = G[g].K / TK;
+            const GemmGroupDev& gg = G[g];
+            const int nk = gg.K / TK;
+            int m0, n0;
+            tile_origin<TN>(gg, t - gg.tile_begin, m0, n0);
+            // a ragged last column tile runs MMAs only as wide as its valid columns (N % 16 == 0)
+            const uint32_t idesc = idesc_n<TN>(min(TN, gg.N - n0));
             const int a = i & 1;
             if (i >= 2) ok = mbar_wait(acce_bar(a), ((i >> 1) - 1) & 1, err, 13);
             if (!ok) break;
@@ -151,11 +156,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 for (int k = 0; k < TK / 16; ++k) {
                     const uint32_t koff = 32u * k;
                     const uint64_t ahi = sw128_desc(sAhi(s) + koff), whi = sw128_desc(sWhi(s) + koff);
-                    mma_bf16<TN>(acc, ahi, whi, (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_bf16_desc(acc, ahi, whi, idesc, (kb > 0 || k > 0) ? 1u : 0u);
                     if (P == 3) {
                         const uint64_t alo = sw128_desc(sAlo(s) + koff), wlo = sw128_desc(sWlo(s) + koff);
-                        mma_bf16<TN>(acc, alo, whi, 1u);
-                        mma_bf16<TN>(acc, ahi, wlo, 1u);
+                        mma_bf16_desc(acc, alo, whi, idesc, 1u);
+                        mma_bf16_desc(acc, ahi, wlo, idesc, 1u);
                     }
                 }
                 mma_commit(empty_bar(s));
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             const int row = m0 + q * 32 + lane;
             const uint32_t lane_addr = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-            for (int c = 0; c < TN; c += 32) {
+            for (int c = 0; c < TN && n0 + c < gg.N; c += 32) {   // columns past N were not computed
                 uint32_t r[32];
                 tmem_ld32(lane_addr + (uint32_t)c, r);
                 const int col = n0 + c;

@@ -17,7 +17,8 @@ namespace bpm {
 constexpr double kMu0 = 1.25663706143591729e-6;       // 4 pi 1e-7 T m / A
 constexpr double kGammaPs = 1.76085963023e-1;         // rad / (ps T)
 constexpr int kMaxNodes = 8192;
-constexpr int kNodePad = 64;                           // n_pad multiple (3 n_pad is a multiple of 64)
+constexpr int kNodePad = 32;                           // n_pad multiple: whole 32-row exchange slices
+constexpr int kKPad = 64;                              // demag GEMM K multiple (one 128-byte BF16 k-block)
 constexpr int kIslandPad = 128;                        // batch rows padded to the GEMM M tile
 
 void set_error(const char* fmt, ...);
@@ -41,6 +42,9 @@ void set_error(const char* fmt, ...);
 // Device-resident operators of one island mesh.
 struct Mesh {
     int n = 0, n_pad = 0, n_tets = 0, nb = 0, nnz = 0;
+    // demag GEMM width: the operand row of an island holds its three component planes
+    // [c n_pad, c n_pad + n) and zeros up to k_pad = 3 n_pad rounded up to kKPad
+    int k_pad = 0;
     // per node (padded to n_pad; padding nodes have w = 0 and no neighbours)
     float4* node_pos = nullptr;   // x, y, z (nm), w_i = V_i / sum V
     float4* node_mat = nullptr;   // 2 Ku_i / Ms_i (T), Ms_i (MA/m), 0, 0
@@ -49,8 +53,9 @@ struct Mesh {
     int n_slices = 0;
     int* sell_off = nullptr;      // [n_slices + 1] first entry of each slice
     int2* sell_ent = nullptr;     // (col, float bits of val), entry e of row 32 s + l at off[s] + 32 e + l
-    // demag operator -mu0*1e6*N, row c*n_pad+i, column c'*n_pad+k (T per MA/m)
-    float* N32 = nullptr;         // [K][K]
+    // demag operator -mu0*1e6*N, row c*n_pad+i, column c'*n_pad+k (T per MA/m); rows and
+    // columns from 3 n_pad to k_pad are zero
+    float* N32 = nullptr;         // [K][K], K = k_pad
     __nv_bfloat16* Nhi = nullptr; // [K][K]
     __nv_bfloat16* Nlo = nullptr; // [K][K]
     double* N64 = nullptr;        // [3n][3n] compact, H = -N M (only with BPM_MESH_KEEP_F64)
@@ -59,7 +64,7 @@ struct Mesh {
     std::vector<float> exch_val;  // c_ij per CSR entry (0 on the diagonal)
     std::vector<double> V, Ms, Ku;
     bpm_mesh_info info{};
-    int K() const { return 3 * n_pad; }
+    int K() const { return k_pad; }
 };
 
 struct HeadMap {

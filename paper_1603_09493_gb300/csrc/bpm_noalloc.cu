@@ -152,6 +152,7 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
     a.B = B;
     a.n = n;
     a.n_pad = np;
+    a.kp = K;
     a.node_pos = M->node_pos;
     a.node_mat = M->node_mat;
     a.sell_off = M->sell_off;

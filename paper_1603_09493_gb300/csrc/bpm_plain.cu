@@ -72,9 +72,10 @@ extern "C" int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, con
     }
     BPM_CK(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
-    int nmax = 0;
-    for (int b = 0; b < B; ++b) nmax = std::max(nmax, ctx->meshes[isl[b].mesh_id]->n_pad);
-    const size_t S = 3 * (size_t)nmax;
+    // one region per buffer, each large enough for a state [3][n_pad] and a GEMM row [k_pad]
+    int kmax = 0;
+    for (int b = 0; b < B; ++b) kmax = std::max(kmax, ctx->meshes[isl[b].mesh_id]->K());
+    const size_t S = (size_t)kmax;
     float *buf = nullptr, *scal = nullptr;
     int *iscal = nullptr;
     long long* interval = nullptr;
@@ -103,6 +104,7 @@ extern "C" int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, con
         a.B = 1;
         a.n = n;
         a.n_pad = np;
+        a.kp = K;
         a.node_pos = M->node_pos;
         a.node_mat = M->node_mat;
         a.sell_off = M->sell_off;

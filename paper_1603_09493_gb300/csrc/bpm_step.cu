@@ -73,7 +73,7 @@ __device__ __forceinline__ float3 eff_field(const StepArgs& a, int b, int i, flo
     // independent per-node loads first, so that their latency overlaps the exchange gather
     float3 hdv = f3(0, 0, 0);
     if (mask & BPM_TERM_DEMAG) {
-        const float* hd = a.Hd + (size_t)b * 3 * np + i;
+        const float* hd = a.Hd + (size_t)b * a.kp + i;
         hdv = f3(hd[0], hd[np], hd[2 * np]);
     }
     const float4 pos = __ldg(a.node_pos + i);
@@ -117,8 +117,7 @@ __device__ __forceinline__ float3 llg_rhs(float3 m, float3 B, float alpha, float
 }
 
 __device__ __forceinline__ void write_gemm_input(const StepArgs& a, int b, int i, float3 v, float msi) {
-    const size_t K = 3 * (size_t)a.n_pad;
-    size_t o = (size_t)b * K + i;
+    size_t o = (size_t)b * a.kp + i;
     float x[3] = {msi * v.x, msi * v.y, msi * v.z};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -256,6 +255,212 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_stage2_groups(const __grid_co
     stage2_body(G.a[g], blockIdx.x - G.block_begin[g], j, red);
 }
 
+// ---------------------------------------------------------------------------
+// Two (IPB) islands per CTA: both islands' states are staged in shared memory,
+// one pass over a node's sliced-ELL entries serves both exchange sums, and the
+// node data are loaded once.  The per-island arithmetic is that of eff_field,
+// term by term in the same order.
+// ---------------------------------------------------------------------------
+
+// exchange sums sum_e v_e (m_q[col_e] - m_q[i]) of node i for the IPB staged islands
+template <int IPB>
+__device__ __forceinline__ void exchange_sums(const StepArgs& a, int i, const float* sm, const float3 (&mi)[IPB],
+                                              float3 (&bex)[IPB]) {
+    const int np = a.n_pad, S = 3 * np;
+    const int s = i >> 5, l = i & 31;
+    const int off = __ldg(a.sell_off + s);
+    const int nw = (__ldg(a.sell_off + s + 1) - off) >> 5;
+    const int2* ep = a.sell_ent + off + l;
+    float bx[IPB], by[IPB], bz[IPB];
+#pragma unroll
+    for (int q = 0; q < IPB; ++q) bx[q] = by[q] = bz[q] = 0.f;
+#pragma unroll 4
+    for (int e = 0; e < nw; ++e) {
+        const int2 c = __ldg(ep + 32 * e);
+        const float v = __int_as_float(c.y);
+#pragma unroll
+        for (int q = 0; q < IPB; ++q) {
+            const float* sq = sm + q * S;
+            bx[q] += v * (sq[c.x] - mi[q].x);
+            by[q] += v * (sq[np + c.x] - mi[q].y);
+            bz[q] += v * (sq[2 * np + c.x] - mi[q].z);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPB; ++q) bex[q] = f3(bx[q], by[q], bz[q]);
+}
+
+// effective field of island b at node i from its exchange sum and the local terms
+__device__ __forceinline__ float3 field_from_sums(const StepArgs& a, float3 mi, float3 bex, float3 hdv, float4 p0,
+                                                  float4 p1, float4 p2, float4 pos, float an0, float ramp, float xh,
+                                                  unsigned mask) {
+    float3 B = f3(0, 0, 0);
+    if (mask & BPM_TERM_EXCHANGE) B = B + p0.x * bex;
+    if (mask & BPM_TERM_ANISOTROPY) {
+        float3 u = f3(p1.x, p1.y, p1.z);
+        float an = an0 * p0.y;
+        B = B + (an * dot3(mi, u)) * u;
+    }
+    if (mask & BPM_TERM_DEMAG) B = B + hdv;
+    if ((mask & BPM_TERM_HEAD) && a.map) {
+        B = B + ramp * trilinear(a, pos.x + p1.w - xh, pos.y + p2.x, pos.z);
+    }
+    if (mask & BPM_TERM_UNIFORM) {
+        B = B + ramp * f3(a.uni[0], a.uni[1], a.uni[2]) + f3(p2.y, p2.z, p2.w);
+    }
+    return B;
+}
+
+__device__ __forceinline__ float3 load_hd(const StepArgs& a, int b, int i) {
+    const float* hd = a.Hd + (size_t)b * a.kp + i;
+    return f3(hd[0], hd[a.n_pad], hd[2 * a.n_pad]);
+}
+
+// predictor of islands b0 .. b0 + nb - 1 (nb <= IPB); sp: [IPB][3] island parameters in smem
+template <int IPB>
+__device__ __forceinline__ void stage1_multi(const StepArgs& a, int b0, int j, float4* sp) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    const int np = a.n_pad, S = 3 * np;
+    const int nb = min(IPB, a.B - b0);
+    if ((int)threadIdx.x < 3 * nb) sp[threadIdx.x] = a.isl[3 * b0 + threadIdx.x];
+    const double t = step_time(a, j);
+    const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
+    const float xh = a.x0 + a.v_nm_ps * (float)t;
+    for (int q = 0; q < nb; ++q) stage_state(a.m + (size_t)(b0 + q) * S, sm + q * S, np);
+    const float hf = (float)a.h;
+    const unsigned mask = a.mask;
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        float3 mi[IPB], bex[IPB], hdv[IPB];
+#pragma unroll
+        for (int q = 0; q < IPB; ++q) {
+            mi[q] = f3(sm[q * S + i], sm[q * S + np + i], sm[q * S + 2 * np + i]);
+            hdv[q] = (mask & BPM_TERM_DEMAG) && q < nb ? load_hd(a, b0 + q, i) : f3(0, 0, 0);
+        }
+        const float4 pos = __ldg(a.node_pos + i);
+        const float4 nm = __ldg(a.node_mat + i);
+        if (mask & BPM_TERM_EXCHANGE) exchange_sums<IPB>(a, i, sm, mi, bex);
+#pragma unroll
+        for (int q = 0; q < IPB; ++q) {
+            if (q < nb) {
+            const int b = b0 + q;
+            const size_t base = (size_t)b * S;
+            const float4 p0 = sp[3 * q], p1 = sp[3 * q + 1], p2 = sp[3 * q + 2];
+            float3 B = field_from_sums(a, mi[q], bex[q], hdv[q], p0, p1, p2, pos, nm.x, ramp, xh, mask);
+            float3 f = llg_rhs(mi[q], B, a.alpha, a.gp);
+            float3 v = normalize3(mi[q] + hf * f);
+            a.k1[base + i] = f.x;
+            a.k1[base + np + i] = f.y;
+            a.k1[base + 2 * np + i] = f.z;
+            a.ms[base + i] = v.x;
+            a.ms[base + np + i] = v.y;
+            a.ms[base + 2 * np + i] = v.z;
+            write_gemm_input(a, b, i, v, nm.y * p0.z);
+            }
+        }
+    }
+}
+
+// corrector and switch detectors of islands b0 .. b0 + nb - 1; red: [IPB][NT / 32]
+template <int IPB>
+__device__ __forceinline__ void stage2_multi(const StepArgs& a, int b0, int j, float4* sp, float* red) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    const int np = a.n_pad, S = 3 * np;
+    const int nb = min(IPB, a.B - b0);
+    if ((int)threadIdx.x < 3 * nb) sp[threadIdx.x] = a.isl[3 * b0 + threadIdx.x];
+    const double t = step_time(a, j) + a.h;
+    const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
+    const float xh = a.x0 + a.v_nm_ps * (float)t;
+    for (int q = 0; q < nb; ++q) stage_state(a.ms + (size_t)(b0 + q) * S, sm + q * S, np);
+    const float hh = 0.5f * (float)a.h;
+    const unsigned mask = a.mask;
+    __syncthreads();
+    float mzp[IPB];
+#pragma unroll
+    for (int q = 0; q < IPB; ++q) mzp[q] = 0.f;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        float3 mi[IPB], bex[IPB], hdv[IPB];
+#pragma unroll
+        for (int q = 0; q < IPB; ++q) {
+            mi[q] = f3(sm[q * S + i], sm[q * S + np + i], sm[q * S + 2 * np + i]);
+            hdv[q] = (mask & BPM_TERM_DEMAG) && q < nb ? load_hd(a, b0 + q, i) : f3(0, 0, 0);
+        }
+        const float4 pos = __ldg(a.node_pos + i);
+        const float4 nm = __ldg(a.node_mat + i);
+        if (mask & BPM_TERM_EXCHANGE) exchange_sums<IPB>(a, i, sm, mi, bex);
+#pragma unroll
+        for (int q = 0; q < IPB; ++q) {
+            if (q < nb) {
+            const int b = b0 + q;
+            const size_t base = (size_t)b * S;
+            const float4 p0 = sp[3 * q], p1 = sp[3 * q + 1], p2 = sp[3 * q + 2];
+            const float3 mn = f3(a.m[base + i], a.m[base + np + i], a.m[base + 2 * np + i]);
+            const float3 f1 = f3(a.k1[base + i], a.k1[base + np + i], a.k1[base + 2 * np + i]);
+            float3 B = field_from_sums(a, mi[q], bex[q], hdv[q], p0, p1, p2, pos, nm.x, ramp, xh, mask);
+            float3 f2 = llg_rhs(mi[q], B, a.alpha, a.gp);
+            float3 v = normalize3(mn + hh * (f1 + f2));
+            a.m[base + i] = v.x;
+            a.m[base + np + i] = v.y;
+            a.m[base + 2 * np + i] = v.z;
+            write_gemm_input(a, b, i, v, nm.y * p0.z);
+            mzp[q] += pos.w * v.z;
+            }
+        }
+    }
+    // fixed-order block sums, one per island
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < IPB; ++q) {
+        float v = mzp[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q * nw + (threadIdx.x >> 5)] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)nb) {
+        const int q = threadIdx.x, b = b0 + q;
+        float mz = 0.f;
+        for (int w = 0; w < nw; ++w) mz += red[q * nw + w];
+        float prev = a.mz_prev[b];
+        if (!a.crossed[b] && mz <= 0.f) {
+            double d = (double)prev - (double)mz;
+            double frac = d > 0 ? (double)prev / d : 1.0;
+            a.t_sw[b] = (float)(t - a.h + a.h * frac);
+            a.crossed[b] = 1;
+        }
+        a.mz_prev[b] = mz;
+        if (!isfinite(mz)) a.status[b] |= BPM_ISLAND_NONFINITE;
+    }
+}
+
+constexpr int kMultiNT = 256, kMultiIPB = 2;
+// 4 CTAs (8 islands) per SM: up to 64 registers a thread; 2 x 18.8 KB of state per CTA at 1568 nodes
+constexpr int kMultiMinBlocks = 4;
+
+__global__ void __launch_bounds__(kMultiNT, kMultiMinBlocks) k_stage1m(StepArgs a, int j) {
+    __shared__ float4 sp[3 * kMultiIPB];
+    stage1_multi<kMultiIPB>(a, kMultiIPB * blockIdx.x, j, sp);
+}
+__global__ void __launch_bounds__(kMultiNT, kMultiMinBlocks) k_stage2m(StepArgs a, int j) {
+    __shared__ float4 sp[3 * kMultiIPB];
+    __shared__ float red[kMultiIPB * kMultiNT / 32];
+    stage2_multi<kMultiIPB>(a, kMultiIPB * blockIdx.x, j, sp, red);
+}
+__global__ void __launch_bounds__(kMultiNT, kMultiMinBlocks) k_stage1m_groups(const __grid_constant__ StageGroups G,
+                                                                             int j) {
+    __shared__ float4 sp[3 * kMultiIPB];
+    const int g = stage_group(G);
+    stage1_multi<kMultiIPB>(G.a[g], kMultiIPB * (blockIdx.x - G.block_begin[g]), j, sp);
+}
+__global__ void __launch_bounds__(kMultiNT, kMultiMinBlocks) k_stage2m_groups(const __grid_constant__ StageGroups G,
+                                                                             int j) {
+    __shared__ float4 sp[3 * kMultiIPB];
+    __shared__ float red[kMultiIPB * kMultiNT / 32];
+    const int g = stage_group(G);
+    stage2_multi<kMultiIPB>(G.a[g], kMultiIPB * (blockIdx.x - G.block_begin[g]), j, sp, red);
+}
+
 __global__ void __launch_bounds__(kStepThreads) k_init(StepArgs a) {
     __shared__ float red[kStepThreads / 32];
     const int b = blockIdx.x;
@@ -320,12 +525,20 @@ int configure_step_kernels() {
     BPM_CK(cudaFuncSetAttribute(k_stage2_groups<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage2_groups<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage2_groups<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem2 = kMultiIPB * smem;
+    BPM_CK(cudaFuncSetAttribute(k_stage1m, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    BPM_CK(cudaFuncSetAttribute(k_stage2m, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    BPM_CK(cudaFuncSetAttribute(k_stage1m_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    BPM_CK(cudaFuncSetAttribute(k_stage2m_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
     return BPM_OK;
 }
 
-int stage_blocks_per_sm(int threads, size_t smem, int* blocks) {
+int stage_blocks_per_sm(int threads, int ipb, size_t smem, int* blocks) {
     int b1 = 0, b2 = 0;
-    if (threads == 128) {
+    if (ipb == kMultiIPB) {
+        BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_stage1m_groups, kMultiNT, smem));
+        BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_stage2m_groups, kMultiNT, smem));
+    } else if (threads == 128) {
         BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_stage1_groups<128>, 128, smem));
         BPM_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_stage2_groups<128>, 128, smem));
     } else if (threads == 512) {
@@ -339,9 +552,13 @@ int stage_blocks_per_sm(int threads, size_t smem, int* blocks) {
     return BPM_OK;
 }
 
+int stage_islands_per_cta(const StepArgs& a) { return a.ipb == kMultiIPB ? kMultiIPB : 1; }
+
 void launch_stage1(const StepArgs& a, int j, cudaStream_t s) {
     const size_t sm = stage_smem_bytes(a);
-    if (a.threads == 128)
+    if (a.ipb == kMultiIPB)
+        k_stage1m<<<(a.B + kMultiIPB - 1) / kMultiIPB, kMultiNT, kMultiIPB * sm, s>>>(a, j);
+    else if (a.threads == 128)
         k_stage1<128><<<a.B, 128, sm, s>>>(a, j);
     else if (a.threads == 512)
         k_stage1<512><<<a.B, 512, sm, s>>>(a, j);
@@ -350,7 +567,9 @@ void launch_stage1(const StepArgs& a, int j, cudaStream_t s) {
 }
 void launch_stage2(const StepArgs& a, int j, cudaStream_t s) {
     const size_t sm = stage_smem_bytes(a);
-    if (a.threads == 128)
+    if (a.ipb == kMultiIPB)
+        k_stage2m<<<(a.B + kMultiIPB - 1) / kMultiIPB, kMultiNT, kMultiIPB * sm, s>>>(a, j);
+    else if (a.threads == 128)
         k_stage2<128><<<a.B, 128, sm, s>>>(a, j);
     else if (a.threads == 512)
         k_stage2<512><<<a.B, 512, sm, s>>>(a, j);
@@ -359,7 +578,9 @@ void launch_stage2(const StepArgs& a, int j, cudaStream_t s) {
 }
 void launch_stage1_groups(const StageGroups& G, int threads, size_t smem, int j, cudaStream_t s) {
     const int blocks = G.block_begin[G.ng];
-    if (threads == 128)
+    if (G.a[0].ipb == kMultiIPB)
+        k_stage1m_groups<<<blocks, kMultiNT, smem, s>>>(G, j);
+    else if (threads == 128)
         k_stage1_groups<128><<<blocks, 128, smem, s>>>(G, j);
     else if (threads == 512)
         k_stage1_groups<512><<<blocks, 512, smem, s>>>(G, j);
@@ -368,7 +589,9 @@ void launch_stage1_groups(const StageGroups& G, int threads, size_t smem, int j,
 }
 void launch_stage2_groups(const StageGroups& G, int threads, size_t smem, int j, cudaStream_t s) {
     const int blocks = G.block_begin[G.ng];
-    if (threads == 128)
+    if (G.a[0].ipb == kMultiIPB)
+        k_stage2m_groups<<<blocks, kMultiNT, smem, s>>>(G, j);
+    else if (threads == 128)
         k_stage2_groups<128><<<blocks, 128, smem, s>>>(G, j);
     else if (threads == 512)
         k_stage2_groups<512><<<blocks, 512, smem, s>>>(G, j);

@@ -6,6 +6,7 @@ namespace bpm {
 
 struct StepArgs {
     int B, n, n_pad;
+    int kp;                   // row stride of Hd and the GEMM operand (k_pad >= 3 n_pad)
     const float4* node_pos;   // [n_pad] x, y, z, w
     const float4* node_mat;   // [n_pad] 2Ku/Ms (T), Ms (MA/m)
     const int* sell_off;
@@ -18,8 +19,8 @@ struct StepArgs {
     float* m;                 // [Bp][3][n_pad]
     float* ms;                // predictor state m*
     float* k1;                // predictor slope
-    const float* Hd;          // demag field of the GEMM input state, tesla
-    float* A32;               // GEMM input (FP32), [Bp][3 n_pad], Ms * m in MA/m
+    const float* Hd;          // demag field of the GEMM input state, tesla, [Bp][kp]
+    float* A32;               // GEMM input (FP32), [Bp][kp], Ms * m in MA/m (planes at c n_pad)
     __nv_bfloat16* Ahi;       // GEMM input BF16 hi/lo split
     __nv_bfloat16* Alo;
     int prec;
@@ -35,12 +36,14 @@ struct StepArgs {
     float uni[3];
     unsigned mask;
     int threads;              // CTA size of the stage kernels: 128, 256 or 512 (autotuned)
+    int ipb;                  // islands per stage CTA: 1, or 2 (256 threads; autotuned)
 };
 
 constexpr int kStepThreads = 256;
 
 // one stage launch over several mesh groups of a batch: CTAs
-// [block_begin[g], block_begin[g + 1]) integrate the islands of group g.  Passed
+// [block_begin[g], block_begin[g + 1]) integrate the islands of group g (one or
+// two islands per CTA, as a.ipb of the groups says; all groups of a launch agree).  Passed
 // by value (a grid-constant kernel parameter, under 10 KB); the groups of one
 // launch share the CTA size, and the dynamic shared memory is the largest
 // group's.
@@ -56,8 +59,11 @@ void launch_stage2(const StepArgs& a, int j, cudaStream_t s);
 void launch_stage1_groups(const StageGroups& G, int threads, size_t smem, int j, cudaStream_t s);
 void launch_stage2_groups(const StageGroups& G, int threads, size_t smem, int j, cudaStream_t s);
 size_t stage_smem_bytes(const StepArgs& a);
-// resident CTAs per SM of the grouped stage kernels at this CTA size and shared memory
-int stage_blocks_per_sm(int threads, size_t smem, int* blocks);
+// resident CTAs per SM of the grouped stage kernels at this CTA size, islands per CTA and
+// shared memory
+int stage_blocks_per_sm(int threads, int ipb, size_t smem, int* blocks);
+// islands per stage CTA of these arguments (1 or 2)
+int stage_islands_per_cta(const StepArgs& a);
 void launch_init(const StepArgs& a, cudaStream_t s);
 void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaStream_t s);
 void launch_interval_tick(long long* interval, cudaStream_t s);

@@ -105,6 +105,25 @@ struct Idesc {
                                       | ((uint32_t)(TM >> 4) << 24);
 };
 
+// the descriptor for an MMA n columns wide (16 <= n <= TN, n % 16 == 0)
+template <int TN>
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+    return (Idesc<TN>::value & ~(0x3Fu << 17)) | ((uint32_t)(n >> 3) << 17);
+}
+
+// D[tmem] (+)= A[adesc] * B[bdesc]^T with a run-time instruction descriptor
+__device__ __forceinline__ void mma_bf16_desc(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 template <int TN>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
     asm volatile(

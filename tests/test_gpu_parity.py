@@ -219,9 +219,11 @@ def test_autotuner_choices_do_not_change_results(ctx, small, headmap):
     p = synth.RunParams(dt_ps=0.1, substeps=8, alpha=0.1, rise_ps=10.0, use_map=True,
                         uniform_T=synth.uniform_field(0.7, 170.0))
     outs = []
-    for tn, nt in [(256, 256), (128, 128), (256, 512), (128, 256)]:
+    # (tile width, stage CTA size, GEMM tile order, islands per stage CTA)
+    for tn, nt, ras, ipb in [(256, 256, L.RASTER_AUTO, 1), (128, 128, L.RASTER_N, 1), (256, 512, L.RASTER_M, 1),
+                             (128, 256, L.RASTER_AUTO, 1), (256, 256, L.RASTER_N, 2), (128, 256, L.RASTER_M, 2)]:
         with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
-            bt.set_tuning(tn, nt)
+            bt.set_tuning(tn, nt, ras, ipb)
             bt.advance(20)
             outs.append(bt.read())
     for o in outs[1:]:
@@ -230,7 +232,33 @@ def test_autotuner_choices_do_not_change_results(ctx, small, headmap):
     with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
         t = bt.autotune(reps=2)
         assert t["gemm_tile_n"] in (128, 256) and t["stage_threads"] in (128, 256, 512)
+        assert t["gemm_raster"] in (0, 1, 2) and t["stage_islands"] in (1, 2)
         assert t["gemm_ms"] > 0 and t["stage_ms"] > 0
         bt.set_state(None, 0.0)
         bt.advance(20)
         assert np.array_equal(bt.read()["m"], outs[0]["m"])
+
+
+def test_two_islands_per_cta_odd_groups(ctx, small, headmap):
+    # two islands per stage CTA over two mesh groups of odd sizes (the last CTA
+    # of each group holds one island): the same m and switch data as one island
+    # per CTA, for the one-group launch and the grouped launch
+    mesh, mats, ops, mid = small
+    hm, hid = headmap
+    mid2 = ctx.mesh_upload(synth.layered_island_mesh(7.0, 6.0, 4.0, rings=2, hard_slabs=9, soft_slabs=6, seed=5),
+                           mats)
+    p = synth.RunParams(dt_ps=0.1, substeps=8, alpha=0.1, rise_ps=10.0, use_map=True,
+                        uniform_T=synth.uniform_field(0.7, 170.0))
+    one = synth.jittered_islands(101, seed=73, mesh_id=mid)
+    two = synth.Islands.concat([one, synth.jittered_islands(57, seed=74, mesh_id=mid2)])
+    for isl in (one, two):
+        outs = []
+        for ipb in (1, 2):
+            with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+                bt.set_tuning(256, 256, L.RASTER_AUTO, ipb)
+                bt.advance(20)
+                outs.append(bt.read())
+        assert np.all(outs[1]["status"] == 0)
+        assert np.array_equal(outs[1]["m"], outs[0]["m"])
+        assert np.array_equal(outs[1]["switched"], outs[0]["switched"])
+        assert np.abs(outs[1]["mz"] - outs[0]["mz"]).max() <= 1e-6
