@@ -122,8 +122,8 @@ def gemm_peak(pk):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum \
 #       --clock-control none -k regex:k_gemm_grouped -s 10 -c 2 --csv \
 #       python bench.py --steps 2 --warmup 1 --no-cpu --no-e2e --no-extras --no-autotune
-# (k_gemm_grouped<3,256>, M-major tile order).  Remove an entry when the kernel changes.
-NCU_GEMM_TRAFFIC = {}
+# (k_gemm_grouped<3,256,32>, N-major tile order).  Remove an entry when the kernel changes.
+NCU_GEMM_TRAFFIC = {(1, 4096, 1547): 412.97e6 + 60.92e6}
 
 
 def gemm_traffic(prec, B, n):

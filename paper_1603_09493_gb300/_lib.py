@@ -61,6 +61,7 @@ RASTER_AUTO, RASTER_M, RASTER_N = 0, 1, 2
 
 class bpm_tuning(ctypes.Structure):
     _fields_ = [("gemm_tile_n", c_int32), ("stage_threads", c_int32), ("gemm_raster", c_int32), ("stage_islands", c_int32),
+                ("gemm_k_block", c_int32), ("reserved", c_int32),
                 ("gemm_ms", c_double), ("stage_ms", c_double)]
 
 

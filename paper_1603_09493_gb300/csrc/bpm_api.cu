@@ -53,6 +53,7 @@ struct bpm_batch {
     std::vector<cudaEvent_t> ev;
     int tile_n = 256;                 // demag GEMM output columns per CTA
     int raster = BPM_RASTER_AUTO;     // demag GEMM tile order
+    int k_block = 32;                 // demag GEMM K depth per pipeline stage
     GroupedGemm gg;                   // tensor-core demag GEMM over all groups (BF16 precisions)
 };
 
@@ -91,7 +92,7 @@ int setup_grouped_gemm(bpm_batch* bt) {
         ops.push_back(GemmOperands{g.Ahi, g.Alo, g.mesh->Nhi, g.mesh->Nlo, g.Hd, g.Bp, K, K});
     }
     return grouped_gemm_setup(&bt->gg, ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1, bt->raster,
-                              bt->ctx->l2_bytes);
+                              bt->k_block, bt->ctx->l2_bytes);
 }
 
 // demag GEMM of every group's current operand A -> Hd: one persistent launch
@@ -604,7 +605,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         for (int c = 0; c < 3; ++c) a.uni[c] = p->uniform_T[c];
         a.mask = p->term_mask;
         a.threads = 256;
-        a.ipb = 1;
+        a.ipb = 2;
     }
     if (r == BPM_OK && bt->groups.size() > 1) {
         const int ns = (int)std::min<size_t>(4, bt->groups.size());
@@ -918,15 +919,17 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
     if (!bt || !t || (t->gemm_tile_n != 128 && t->gemm_tile_n != 256) ||
         (t->stage_threads != 128 && t->stage_threads != 256 && t->stage_threads != 512) ||
         (t->gemm_raster != BPM_RASTER_AUTO && t->gemm_raster != BPM_RASTER_M && t->gemm_raster != BPM_RASTER_N) ||
-        t->stage_islands < 0 || t->stage_islands > 2 || (t->stage_islands == 2 && t->stage_threads != 256)) {
+        t->stage_islands < 0 || t->stage_islands > 2 || (t->stage_islands == 2 && t->stage_threads != 256) ||
+        (t->gemm_k_block != 0 && t->gemm_k_block != 32 && t->gemm_k_block != 64)) {
         set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512, gemm_raster 0|1|2, "
-                  "stage_islands 0|1|2 with 2 only at 256 threads)");
+                  "stage_islands 0|1|2 with 2 only at 256 threads, gemm_k_block 0|32|64)");
         return BPM_ERR_ARG;
     }
     BPM_TRY(ensure_device(bt->ctx));
     BPM_CK(cudaStreamSynchronize(bt->ctx->stream));
     bt->tile_n = t->gemm_tile_n;
     bt->raster = t->gemm_raster;
+    bt->k_block = t->gemm_k_block == 64 ? 64 : 32;
     for (auto& g : bt->groups) {
         g.args.threads = t->stage_threads;
         g.args.ipb = t->stage_islands == 2 ? 2 : 1;
@@ -943,29 +946,32 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
     }
     const int tiles[2] = {256, 128};
     const int rasters[3] = {BPM_RASTER_AUTO, BPM_RASTER_M, BPM_RASTER_N};
+    const int kblocks[2] = {64, 32};
     const int threads[3] = {256, 128, 512};
     const bool tc = tensor_core_precision(bt);
     double best_g = 1e300, best_s = 1e300;
-    int bt_n = 256, bt_r = BPM_RASTER_AUTO, bt_t = 256;
+    int bt_n = 256, bt_r = BPM_RASTER_AUTO, bt_t = 256, bt_k = 64;
     // the GEMM candidates at the default stage CTA size, then the stage CTA sizes at the best GEMM
     for (int ti = 0; ti < (tc ? 2 : 1); ++ti)
-        for (int ri = 0; ri < (tc ? 3 : 1); ++ri) {
-            bpm_tuning t{tiles[ti], 256, rasters[ri], 1, 0, 0};
-            BPM_TRY(bpm_batch_set_tuning(bt, &t));
-            double g = 0, s1 = 0, s2 = 0;
-            BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));   // warm-up
-            BPM_TRY(bpm_batch_kernel_times(bt, reps, &g, &s1, &s2));
-            if (g < best_g) {
-                best_g = g;
-                bt_n = tiles[ti];
-                bt_r = rasters[ri];
+        for (int ri = 0; ri < (tc ? 3 : 1); ++ri)
+            for (int ki = 0; ki < (tc ? 2 : 1); ++ki) {
+                bpm_tuning t{tiles[ti], 256, rasters[ri], 1, kblocks[ki], 0, 0, 0};
+                BPM_TRY(bpm_batch_set_tuning(bt, &t));
+                double g = 0, s1 = 0, s2 = 0;
+                BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));   // warm-up
+                BPM_TRY(bpm_batch_kernel_times(bt, reps, &g, &s1, &s2));
+                if (g < best_g) {
+                    best_g = g;
+                    bt_n = tiles[ti];
+                    bt_r = rasters[ri];
+                    bt_k = kblocks[ki];
+                }
             }
-        }
     // stage candidates: one island per CTA at each CTA size, two islands per 256-thread CTA
     int bt_i = 1;
     for (int hi = 0; hi < 4; ++hi) {
         const int nt = hi < 3 ? threads[hi] : 256, ipb = hi < 3 ? 1 : 2;
-        bpm_tuning t{bt_n, nt, bt_r, ipb, 0, 0};
+        bpm_tuning t{bt_n, nt, bt_r, ipb, bt_k, 0, 0, 0};
         BPM_TRY(bpm_batch_set_tuning(bt, &t));
         double g = 0, s1 = 0, s2 = 0;
         BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));
@@ -976,7 +982,7 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
             bt_i = ipb;
         }
     }
-    bpm_tuning t{bt_n, bt_t, bt_r, bt_i, best_g, best_s};
+    bpm_tuning t{bt_n, bt_t, bt_r, bt_i, bt_k, 0, best_g, best_s};
     BPM_TRY(bpm_batch_set_tuning(bt, &t));
     if (chosen) *chosen = t;
     return BPM_OK;

@@ -28,13 +28,21 @@ using namespace tc;
 
 constexpr int kGThreads = 192;
 
-template <int P, int TN>
+// KB: K depth of a stage (64: 128 B rows, 128-byte swizzle; 32: 64 B rows, 64-byte swizzle)
+template <int P, int TN, int KB>
 struct GCfg {
-    static constexpr int W_TILE = Tile<TN>::W_TILE;
-    static constexpr int stage_bytes = (P == 3 ? 2 : 1) * (A_TILE + W_TILE);
+    static constexpr int A_BYTES = TM * KB * 2;
+    static constexpr int W_BYTES = TN * KB * 2;
+    static constexpr int stage_bytes = (P == 3 ? 2 : 1) * (A_BYTES + W_BYTES);
     static constexpr int stages = (192 * 1024) / stage_bytes;
     static constexpr int smem = stages * stage_bytes + 1024 + 256;
+    static_assert(8 * (2 * stages + 5) + 4 <= 256, "barrier area");
 };
+
+template <int KB>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t addr) {
+    return KB == 64 ? sw128_desc(addr) : sw64_desc(addr);
+}
 
 __device__ __forceinline__ int find_group(const GemmGroupDev* __restrict__ G, int ng, int t) {
     int g = 0;
@@ -51,12 +59,13 @@ __device__ __forceinline__ void tile_origin(const GemmGroupDev& gg, int lt, int&
     n0 = nt * TN;
 }
 
-template <int P, int TN>
+template <int P, int TN, int KB>
 __global__ void __launch_bounds__(kGThreads, 1)
     k_gemm_grouped(const GemmGroupDev* __restrict__ G, int ng, int total_tiles, int* err) {
-    using CF = GCfg<P, TN>;
+    using CF = GCfg<P, TN, KB>;
     constexpr int S = CF::stages;
-    constexpr int W_TILE = CF::W_TILE;
+    constexpr int A_TILE = CF::A_BYTES;
+    constexpr int W_TILE = CF::W_BYTES;
     extern __shared__ uint8_t smem_raw[];
     {   // an earlier launch gave up: skip (decided once per CTA, so that no thread is left at a barrier)
         __shared__ int s_abort;
@@ -112,13 +121,13 @@ __global__ void __launch_bounds__(kGThreads, 1)
             const GemmGroupDev& gg = G[g];
             int m0, n0;
             tile_origin<TN>(gg, t - gg.tile_begin, m0, n0);
-            const int nk = gg.K / TK;
+            const int nk = gg.K / KB;
             for (int kb = 0; kb < nk; ++kb, ++kbg) {
                 const int s = kbg % S;
                 if (kbg >= S) ok = mbar_wait(empty_bar(s), ((kbg / S) - 1) & 1, err, 11);
                 if (!ok) break;
                 mbar_expect_tx(full_bar(s), CF::stage_bytes);
-                const int kc = kb * TK;
+                const int kc = kb * KB;
                 tma_load_2d(sAhi(s), &gg.ahi, kc, m0, full_bar(s));
                 tma_load_2d(sWhi(s), &gg.whi, kc, n0, full_bar(s));
                 if (P == 3) {
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x, ++i) {
             const int g = find_group(G, ng, t);
             const GemmGroupDev& gg = G[g];
-            const int nk = gg.K / TK;
+            const int nk = gg.K / KB;
             int m0, n0;
             tile_origin<TN>(gg, t - gg.tile_begin, m0, n0);
             // a ragged last column tile runs MMAs only as wide as its valid columns (N % 16 == 0)
@@ -153,12 +162,12 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-                for (int k = 0; k < TK / 16; ++k) {
-                    const uint32_t koff = 32u * k;
-                    const uint64_t ahi = sw128_desc(sAhi(s) + koff), whi = sw128_desc(sWhi(s) + koff);
+                for (int k = 0; k < KB / 16; ++k) {
+                    const uint32_t koff = 32u * k;    // 16 BF16 further along the swizzled row
+                    const uint64_t ahi = kmajor_desc<KB>(sAhi(s) + koff), whi = kmajor_desc<KB>(sWhi(s) + koff);
                     mma_bf16_desc(acc, ahi, whi, idesc, (kb > 0 || k > 0) ? 1u : 0u);
                     if (P == 3) {
-                        const uint64_t alo = sw128_desc(sAlo(s) + koff), wlo = sw128_desc(sWlo(s) + koff);
+                        const uint64_t alo = kmajor_desc<KB>(sAlo(s) + koff), wlo = kmajor_desc<KB>(sWlo(s) + koff);
                         mma_bf16_desc(acc, alo, whi, idesc, 1u);
                         mma_bf16_desc(acc, ahi, wlo, idesc, 1u);
                     }
@@ -214,16 +223,17 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
 }
 
-template <int P, int TN>
+template <int P, int TN, int KB>
 int launch_grouped(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err) {
     static bool configured = false;
     if (!configured) {
-        BPM_CK(cudaFuncSetAttribute(k_gemm_grouped<P, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    GCfg<P, TN>::smem));
+        BPM_CK(cudaFuncSetAttribute(k_gemm_grouped<P, TN, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    GCfg<P, TN, KB>::smem));
         configured = true;
     }
     const int grid = std::max(1, std::min(gg.total_tiles, sm_count));
-    k_gemm_grouped<P, TN><<<grid, kGThreads, GCfg<P, TN>::smem, s>>>(gg.d_groups, gg.n_groups, gg.total_tiles, err);
+    k_gemm_grouped<P, TN, KB>
+        <<<grid, kGThreads, GCfg<P, TN, KB>::smem, s>>>(gg.d_groups, gg.n_groups, gg.total_tiles, err);
     BPM_CK(cudaGetLastError());
     return BPM_OK;
 }
@@ -231,7 +241,11 @@ int launch_grouped(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err
 }  // namespace
 
 int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products, int raster,
-                       size_t l2_bytes) {
+                       int k_block, size_t l2_bytes) {
+    if (k_block != 64 && k_block != 32) {
+        set_error("grouped GEMM k-block must be 64 or 32");
+        return BPM_ERR_ARG;
+    }
     if (tile_n != 128 && tile_n != 256) {
         set_error("grouped GEMM tile width must be 128 or 256");
         return BPM_ERR_ARG;
@@ -250,11 +264,11 @@ int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, in
             return BPM_ERR_ARG;
         }
         std::memset(&h[g], 0, sizeof(GemmGroupDev));
-        BPM_TRY(make_bf16_tensor_map(&h[g].ahi, o.Ahi, o.K, o.M, tc::TM));
-        BPM_TRY(make_bf16_tensor_map(&h[g].whi, o.Whi, o.K, o.N, tile_n));
+        BPM_TRY(make_bf16_tensor_map(&h[g].ahi, o.Ahi, o.K, o.M, tc::TM, k_block));
+        BPM_TRY(make_bf16_tensor_map(&h[g].whi, o.Whi, o.K, o.N, tile_n, k_block));
         if (products == 3) {
-            BPM_TRY(make_bf16_tensor_map(&h[g].alo, o.Alo, o.K, o.M, tc::TM));
-            BPM_TRY(make_bf16_tensor_map(&h[g].wlo, o.Wlo, o.K, o.N, tile_n));
+            BPM_TRY(make_bf16_tensor_map(&h[g].alo, o.Alo, o.K, o.M, tc::TM, k_block));
+            BPM_TRY(make_bf16_tensor_map(&h[g].wlo, o.Wlo, o.K, o.N, tile_n, k_block));
         } else {
             h[g].alo = h[g].ahi;
             h[g].wlo = h[g].whi;
@@ -267,10 +281,10 @@ int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, in
         h[g].tiles_m = o.M / tc::TM;
         h[g].tiles_n = (o.N + tile_n - 1) / tile_n;
         h[g].tile_begin = tiles;
-        // AUTO: N-major when the operator (N x K, every split part) does not fit in L2 and
-        // has more rows than the batch operand
-        const size_t w_bytes = (size_t)o.N * o.K * sizeof(__nv_bfloat16) * (products == 3 ? 2 : 1);
-        const bool auto_n = w_bytes > l2_bytes && o.N > o.M;
+        // AUTO: N-major when the operator has more rows than the batch operand, so that the
+        // larger operand is streamed once per launch and the smaller one re-read from L2
+        (void)l2_bytes;
+        const bool auto_n = o.N > o.M;
         h[g].n_major = raster == BPM_RASTER_N || (raster == BPM_RASTER_AUTO && auto_n) ? 1 : 0;
         tiles += h[g].tiles_m * h[g].tiles_n;
     }
@@ -281,6 +295,7 @@ int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, in
     gg->total_tiles = tiles;
     gg->tile_n = tile_n;
     gg->products = products;
+    gg->k_block = k_block;
     return BPM_OK;
 }
 
@@ -295,12 +310,18 @@ int grouped_gemm_launch(cudaStream_t s, const GroupedGemm& gg, int sm_count, int
         set_error("grouped GEMM not set up");
         return BPM_ERR_STATE;
     }
-    if (gg.products == 3) {
-        if (gg.tile_n == 128) return launch_grouped<3, 128>(s, gg, sm_count, err);
-        return launch_grouped<3, 256>(s, gg, sm_count, err);
+    if (gg.k_block == 32) {
+        if (gg.products == 3)
+            return gg.tile_n == 128 ? launch_grouped<3, 128, 32>(s, gg, sm_count, err)
+                                    : launch_grouped<3, 256, 32>(s, gg, sm_count, err);
+        return gg.tile_n == 128 ? launch_grouped<1, 128, 32>(s, gg, sm_count, err)
+                                : launch_grouped<1, 256, 32>(s, gg, sm_count, err);
     }
-    if (gg.tile_n == 128) return launch_grouped<1, 128>(s, gg, sm_count, err);
-    return launch_grouped<1, 256>(s, gg, sm_count, err);
+    if (gg.products == 3)
+        return gg.tile_n == 128 ? launch_grouped<3, 128, 64>(s, gg, sm_count, err)
+                                : launch_grouped<3, 256, 64>(s, gg, sm_count, err);
+    return gg.tile_n == 128 ? launch_grouped<1, 128, 64>(s, gg, sm_count, err)
+                            : launch_grouped<1, 256, 64>(s, gg, sm_count, err);
 }
 
 }  // namespace bpm

@@ -269,7 +269,11 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows) {
+int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows, int box_inner) {
+    if (box_inner != 64 && box_inner != 32) {
+        set_error("TMA box depth must be 64 or 32 elements (got %d)", box_inner);
+        return BPM_ERR_ARG;
+    }
     EncodeTiledFn fn = encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -281,10 +285,12 @@ int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows,
     }
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
-    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    // rows of box_inner BF16 elements: 128 B rows with the 128-byte swizzle, 64 B rows with the 64-byte one
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
+    const CUtensorMapSwizzle sw = box_inner == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);

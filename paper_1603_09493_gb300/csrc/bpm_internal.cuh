@@ -137,13 +137,15 @@ struct GemmOperands {
 };
 struct GroupedGemm {
     GemmGroupDev* d_groups = nullptr;
-    int n_groups = 0, total_tiles = 0, tile_n = 256, products = 3;
+    int n_groups = 0, total_tiles = 0, tile_n = 256, products = 3, k_block = 64;
 };
+// k_block: K depth of one pipeline stage, 64 (128-byte swizzle) or 32 (64-byte swizzle, twice the stages)
 int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products, int raster,
-                       size_t l2_bytes);
+                       int k_block, size_t l2_bytes);
 void grouped_gemm_free(GroupedGemm* gg);
 int grouped_gemm_launch(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err);
-int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows);
+// TMA map of a row-major BF16 [rows][inner] matrix, boxes of box_rows x box_inner (64 or 32)
+int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows, int box_inner = 64);
 
 // demag GEMMs: C[M_rows][Nout] = A[M_rows][K] * W[Nout][K]^T, row strides lda/ldw/ldc (elements)
 int gemm_f32_nt(cudaStream_t s, int M_rows, int Nout, int K, const float* A, int lda,

@@ -95,6 +95,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
     return d;
 }
 
+// the same for 64 B rows with the 64-byte swizzle (8-row groups 512 B apart)
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);       // start address
+    d |= (uint64_t)1 << 16;                        // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512 >> 4) << 32;               // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
+    d |= (uint64_t)4 << 61;                        // 64 B swizzle
+    return d;
+}
+
 // instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128, N = TN
 template <int TN>
 struct Idesc {

@@ -36,10 +36,10 @@ def _state(xyz, B, seed):
     return (m / np.linalg.norm(m, axis=1, keepdims=True)).astype(np.float32)
 
 
-def _demag(ctx, isl, p, prec, m, tile_n=None, raster=L.RASTER_AUTO):
+def _demag(ctx, isl, p, prec, m, tile_n=None, raster=L.RASTER_AUTO, k_block=64):
     with ctx.batch(isl, p, precision=prec) as bt:
         if tile_n is not None:
-            bt.set_tuning(tile_n, 256, raster)
+            bt.set_tuning(tile_n, 256, raster, gemm_k_block=k_block)
         bt.set_state(m, 0.0)
         return bt.field(0.0, L.TERM_DEMAG)
 
@@ -64,6 +64,8 @@ def test_tc_gemm_matches_split_reference_and_fp32(ctx, case, tile_n):
     ref = _demag(ctx, isl, p, L.PREC_BF16X3_REF, m)
     tc3 = _demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n)
     tc1 = _demag(ctx, isl, p, L.PREC_BF16, m, tile_n)
+    assert np.array_equal(_demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n, k_block=32), tc3)
+    assert np.array_equal(_demag(ctx, isl, p, L.PREC_BF16, m, tile_n, k_block=32), tc1)
     scale = np.abs(f32).max()
     K = info["k_pad"]
     acc_bound = (3 * K / 16) * 2.0 ** -23
@@ -101,9 +103,11 @@ def test_grouped_gemm_over_mesh_groups(ctx):
     for tile_n in (256, 128):
         tc3 = _demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n)
         assert np.all(np.isfinite(tc3))
-        # the tile order changes which CTA computes a tile, never its summation
+        # the tile order changes which CTA computes a tile, and the stage depth how the
+        # k16 MMAs are grouped into pipeline stages, never the summation
         for raster in (L.RASTER_M, L.RASTER_N):
             assert np.array_equal(_demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n, raster), tc3)
+        assert np.array_equal(_demag(ctx, isl, p, L.PREC_BF16X3, m, tile_n, L.RASTER_AUTO, 32), tc3)
         for k, msh in enumerate(meshes):
             rows = np.where(isl.mesh_id == mids[k])[0]
             n = msh.n_nodes
