@@ -16,6 +16,8 @@ Modules
   llg       effective field, Heun integrator with renormalisation, switch detector
   mlp       surrogate MLP forward/backward, BCE loss, AdamW
   ber       bit-error-rate formulas of Sec. II.C (Eqs. 1-3)
+  hcrit     critical-field search of Sec. II.C
+  neb       nudged elastic band for the adjacent-track barrier (Sec. II.C, Eq. 3)
 
 Parity status: the full switching dynamics of an island is pinned only
 through its invariants and closed-form special cases (no trajectory is printed

@@ -39,7 +39,7 @@ def test_ber_of_round_multiples_of_sigma():
 
 def test_ber_tot_is_the_sum_of_the_table_columns():
     rows, _ = _rows()
-    for name, tot, targ, prev, adj, _k in rows:
+    for name, tot, targ, prev, adj, _k, _eb0 in rows:
         s = ber.ber_tot(targ, prev, adj)
         # the paper rounds every entry to two digits; one row (centered, 2.84e-3)
         # differs from its printed total by the rounding of the sum
