@@ -173,6 +173,29 @@ def measure_plain(ctx, isl, p, hid, prec, n, islands=8, intervals=2):
             "same_switch_flags": bool(np.array_equal(plain["switched"], mixed["switched"]))}
 
 
+def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400):
+    """Adjacent-track barriers (Sec. II.C, Eq. 3): D islands of the census mesh on
+    the adjacent track (12.7 nm cross-track), head frozen 2 nm into the map, one
+    band of P images each, BF16x3 demag; wall-clock of the bpm_neb_run call."""
+    from paper_1603_09493_gb300 import adjacent, synth
+    isl = synth.jittered_islands(D, seed=4, mesh_id=mid)
+    isl.pos_nm[:, 1] += 12.7
+    p = synth.RunParams(dt_ps=0.1, rise_ps=0.0, v_m_per_s=0.0, x0_nm=2.0, use_map=True)
+    step = adjacent.stable_step(ctx, mid, isl, p, hm)
+    ctx.neb(isl, P, 2, step, 1.0, -1, map_id=hid, head_x_nm=p.x0_nm)           # warm-up
+    t = time.perf_counter()
+    out = adjacent.barriers(ctx, isl, p, n_images=P, max_iters=iters, climb_after=iters // 2, step=step,
+                            map_id=hid, head_map=hm)
+    wall = time.perf_counter() - t
+    kt = out["E_B_kT"]
+    return {"image_updates_per_s": D * P * out["iters"] / wall, "unit": "band-image updates/s", "bands": D,
+            "images": P, "iters": out["iters"], "wall_s": wall, "max_force": out["max_force"],
+            "E_B_kT_median": float(np.median(kt)), "E_B_kT_min": float(np.min(kt)),
+            "ber_adj_median": float(np.median(out["ber_adj"])),
+            "note": "each update: one BF16x3 demag GEMM over all images, energy/field and band kernels; "
+                    "wall-clock incl. buffer setup and convergence checks every 50 updates"}
+
+
 def measure_surrogate(ctx, torch, stream, n_infer=16384, n_train=65536, batch=4096, reps=20):
     """Surrogate MLP 16-256x4-2 (BF16 tensor-core GEMMs): inference evals/s on a
     device-resident screening batch, training samples/s (AdamW steps)."""
@@ -426,6 +449,7 @@ def main(args):
     if not args.no_extras and rank == 0:
         extras["plain"] = measure_plain(ctx, isl, p, hid, prec, n)
         extras["surrogate"] = measure_surrogate(ctx, torch, stream)
+        extras["neb"] = measure_neb(ctx, mid, hm, hid)
     ctx.close()
     if rank != 0:
         return 0

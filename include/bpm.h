@@ -351,6 +351,65 @@ int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int32_t B,
                             const bpm_run_params* p, int32_t n_intervals, float* m, int32_t ld,
                             float* mz);
 
+/* ---------------------------------------------------------------------- */
+/* Energy barrier in the fringing field (Sec. II.C, adjacent-track erasure) */
+/* ---------------------------------------------------------------------- */
+
+/* The paper places the adjacent bit in the head's fringing field (frozen at
+ * the down-track position of the lowest barrier), computes its switching
+ * barrier E_B with the nudged elastic band method, and turns it into
+ * BER_adj = t_write f0 exp(-E_B / kT) (Eq. 3).  A band of n_images states of one
+ * island runs from the +z minimum to the -z minimum; every image is a row of
+ * one batch, so the demag products of all images of all bands are one GEMM.
+ *
+ * Energy (J): E = -sum_i V_i Ms_i (B_quad,i / 2 + B_lin,i) . m_i, with B_quad
+ * the exchange, anisotropy and demag fields and B_lin the head and uniform
+ * fields (the same terms and readings as the time integration).  Band
+ * update of every image at once, in the metric <a,b> = sum_i w_i a_i . b_i
+ * (w_i = V_i / sum V):
+ *   force density g_i = Ms_i B_i_perp (MA/m x T), B_perp the part of the field
+ *                 normal to m_i;
+ *   interior image: g - <g,t> t + spring (|m+ - m| - |m - m-|) t with the
+ *                 improved tangent t (the higher neighbour's side, weighted by
+ *                 the energy differences at an extremum), projected on every
+ *                 node's tangent plane and normalised; the highest interior
+ *                 image takes g - 2 <g,t> t once climbing is on;
+ *   end images:   g (they relax into the minima);
+ *   m_i <- (m_i + step f_i) / |m_i + step f_i|.
+ */
+typedef struct {
+    int32_t  n_images;     /* images per band, end images included (>= 3) */
+    int32_t  max_iters;    /* band updates */
+    int32_t  climb_after;  /* first update with a climbing image; < 0: never */
+    int32_t  precision;    /* BPM_PREC_* of the demag product */
+    int32_t  map_id;       /* head map of the fringing field, or -1 */
+    uint32_t term_mask;    /* BPM_TERM_* */
+    int32_t  check_every;  /* updates between convergence checks (0: 50) */
+    int32_t  pad_;
+    double   step;         /* > 0, per unit of force density (m^3/MJ) */
+    double   spring;       /* >= 0, MA/m x T per unit of weighted distance */
+    double   force_tol;    /* stop once every image's max |force_i| is below it (0: run max_iters) */
+    double   head_x_nm;    /* head position: the map is sampled at x_i + pos_x - head_x, ramp 1 */
+    double   uniform_T[3]; /* uniform applied field (T), added with every island's Hext_T */
+} bpm_neb_params;
+
+/* Relax one band per island.
+ *   isl, D     host island table [D]; all on one mesh; each band uses its
+ *              island's Ms/Ku jitter, axis, position and Hext_T
+ *   m_init     host [D][n_images][3][ld] initial band, or NULL for the great
+ *              circle from +z to -z through +x (uniform states)
+ *   E_path     host [D][n_images] energies of the final band (J), nullable
+ *   E_barrier  host [D] max over interior images of E - E of image 0 (J), nullable
+ *   m_path     host [D][n_images][3][ld] final band, nullable
+ *   iters_done updates run (fewer than max_iters when force_tol was met)
+ *   max_force  max |force_i| over all images at the last check (MA/m x T)
+ * Device buffers are allocated for the call and freed before it returns; the
+ * call synchronises the context stream.  BPM_ERR_ARG on bad arguments,
+ * BPM_ERR_TIMEOUT if a tensor-core GEMM wait timed out. */
+int bpm_neb_run(bpm_ctx* ctx, const bpm_island* isl, int32_t D, const bpm_neb_params* p, const float* m_init,
+                int32_t ld, double* E_path, double* E_barrier, float* m_path, int32_t* iters_done,
+                double* max_force);
+
 #ifdef __cplusplus
 }
 #endif

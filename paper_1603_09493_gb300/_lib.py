@@ -59,6 +59,13 @@ class bpm_train_cfg(ctypes.Structure):
 RASTER_AUTO, RASTER_M, RASTER_N = 0, 1, 2
 
 
+class bpm_neb_params(ctypes.Structure):
+    _fields_ = [("n_images", c_int32), ("max_iters", c_int32), ("climb_after", c_int32), ("precision", c_int32),
+                ("map_id", c_int32), ("term_mask", ctypes.c_uint32), ("check_every", c_int32), ("pad_", c_int32),
+                ("step", c_double), ("spring", c_double), ("force_tol", c_double), ("head_x_nm", c_double),
+                ("uniform_T", c_double * 3)]
+
+
 class bpm_tuning(ctypes.Structure):
     _fields_ = [("gemm_tile_n", c_int32), ("stage_threads", c_int32), ("gemm_raster", c_int32), ("stage_islands", c_int32),
                 ("gemm_k_block", c_int32), ("reserved", c_int32),
@@ -88,6 +95,8 @@ PROTOTYPES = {
     "bpm_batch_set_tuning": (c_int, [c_void_p, POINTER(bpm_tuning)]),
     "bpm_debug_set_gemm_error": (c_int, [c_void_p, c_int32]),
     "bpm_batch_graph_kernels": (c_int, [c_void_p, POINTER(c_int32)]),
+    "bpm_neb_run": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_neb_params), c_void_p, c_int32, c_void_p,
+                            c_void_p, c_void_p, POINTER(c_int32), POINTER(c_double)]),
     "bpm_batch_time": (c_int, [c_void_p, POINTER(c_double)]),
     "bpm_batch_destroy": (c_int, [c_void_p]),
     "bpm_run_batch": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,

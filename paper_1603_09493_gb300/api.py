@@ -147,6 +147,31 @@ class Context:
         L.check(self.lib.bpm_llg_advance_noalloc(self.h, L.ptr(isl), len(isl), byref(q), int(n_intervals),
                                                  L.ptr(m_dev), int(m_dev.shape[-1]), L.ptr(mz_dev)))
 
+    def neb(self, islands, n_images: int, max_iters: int, step: float, spring: float, climb_after: int = -1,
+            precision: int = L.PREC_BF16X3, map_id: int = -1, head_x_nm: float = 0.0, uniform_T=(0.0, 0.0, 0.0),
+            term_mask: int = L.TERM_ALL, m_init=None, force_tol: float = 0.0, check_every: int = 50,
+            want_path: bool = False) -> dict:
+        """Nudged elastic band of one band per island (bpm_neb_run); returns
+        E [D][P] (J), E_B [D] (J), iters, max_force and, with want_path, m [D][P][3][n]."""
+        isl = island_array(islands)
+        D = len(isl)
+        n = self.mesh_info(int(isl["mesh_id"][0]))["n_nodes"]
+        q = L.bpm_neb_params(int(n_images), int(max_iters), int(climb_after), int(precision), int(map_id),
+                             int(term_mask), int(check_every), 0, float(step), float(spring), float(force_tol),
+                             float(head_x_nm), (c_double * 3)(*[float(x) for x in uniform_T]))
+        E = np.zeros((D, n_images), np.float64)
+        EB = np.zeros(D, np.float64)
+        mi = None if m_init is None else np.ascontiguousarray(m_init, np.float32)
+        mp = np.zeros((D, n_images, 3, n), np.float32) if want_path else None
+        it = c_int32()
+        fm = c_double()
+        L.check(self.lib.bpm_neb_run(self.h, L.ptr(isl), D, byref(q), L.ptr(mi), n, L.ptr(E), L.ptr(EB), L.ptr(mp),
+                                     byref(it), byref(fm)))
+        out = dict(E=E, E_B=EB, iters=it.value, max_force=fm.value)
+        if want_path:
+            out["m"] = mp
+        return out
+
     def surrogate(self, sizes, params) -> "Surrogate":
         return Surrogate(self, sizes, params)
 

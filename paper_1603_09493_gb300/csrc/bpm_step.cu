@@ -461,6 +461,182 @@ __global__ void __launch_bounds__(kMultiNT, kMultiMinBlocks) k_stage2m_groups(co
     stage2_multi<kMultiIPB>(G.a[g], kMultiIPB * (blockIdx.x - G.block_begin[g]), j, sp, red);
 }
 
+// ---------------------------------------------------------------------------
+// Nudged elastic band (Sec. II.C, adjacent-track barrier): one CTA per image,
+// image k of band d in row d * P + k.  The head field is frozen at the head
+// position x0 (ramp 1).  Metric: <a, b> = sum_i w_i a_i . b_i, w_i = V_i / sum V.
+// ---------------------------------------------------------------------------
+
+constexpr unsigned kQuadTerms = BPM_TERM_EXCHANGE | BPM_TERM_ANISOTROPY | BPM_TERM_DEMAG;
+constexpr unsigned kLinTerms = BPM_TERM_HEAD | BPM_TERM_UNIFORM;
+
+// fixed-order sum of one double per thread over the CTA; every thread gets the result
+template <int NT>
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();   // red may still be read from a previous call
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    return s;
+}
+
+// total field Bt of every image and its energy
+//   E = -sum_i V_i Ms_i (B_quad,i / 2 + B_lin,i) . m_i   (J; vol_scale = sum V [nm^3] * 1e-21)
+__global__ void __launch_bounds__(kStepThreads) k_neb_energy(StepArgs a, float* __restrict__ Bt,
+                                                             double* __restrict__ E, double vol_scale) {
+    extern __shared__ float4 smem4[];
+    __shared__ double red[kStepThreads / 32];
+    float* sm = reinterpret_cast<float*>(smem4);
+    const int b = blockIdx.x;
+    const int np = a.n_pad;
+    const size_t base = (size_t)b * 3 * np;
+    const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
+    const float xh = a.x0;
+    stage_state(a.m + base, sm, np);
+    __syncthreads();
+    double e = 0.0;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        const float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
+        const float3 Bq = eff_field(a, b, i, mi, sm, p0, p1, p2, 1.f, xh, a.mask & kQuadTerms);
+        const float3 Bl = eff_field(a, b, i, mi, sm, p0, p1, p2, 1.f, xh, a.mask & kLinTerms);
+        const float3 B = Bq + Bl;
+        Bt[base + i] = B.x;
+        Bt[base + np + i] = B.y;
+        Bt[base + 2 * np + i] = B.z;
+        const float msn = __ldg(&a.node_mat[i].y) * p0.z;
+        const float w = __ldg(&a.node_pos[i].w);
+        e += (double)(w * msn) * (double)dot3(0.5f * Bq + Bl, mi);
+    }
+    const double tot = block_sum_d<kStepThreads>(e, red);
+    if (threadIdx.x == 0) E[b] = -vol_scale * tot;
+}
+
+__device__ __forceinline__ float3 perp3(float3 v, float3 m) { return v + (-dot3(v, m)) * m; }
+__device__ __forceinline__ float3 sub3(float3 x, float3 y) { return f3(x.x - y.x, x.y - y.y, x.z - y.z); }
+__device__ __forceinline__ float3 load_state(const float* m, size_t base, int np, int i) {
+    return f3(m[base + i], m[base + np + i], m[base + 2 * np + i]);
+}
+
+// one band update of every image (Jacobi: neighbours from m_in, result to m_out)
+__global__ void __launch_bounds__(kStepThreads) k_neb_step(StepArgs a, NebArgs nb) {
+    __shared__ double red[kStepThreads / 32];
+    __shared__ int s_ci;
+    const int b = blockIdx.x, P = nb.P, d = b / P, k = b - d * P;
+    const int np = a.n_pad;
+    const size_t S = 3 * (size_t)np, base = (size_t)b * S;
+    const float msc = a.isl[3 * b].z;
+    const bool end = (k == 0 || k == P - 1);
+    // climbing image of this band: the interior image of highest energy
+    if (threadIdx.x == 0) {
+        int ci = -1;
+        if (nb.climb) {
+            double emax = -1e300;
+            for (int q = 1; q < P - 1; ++q) {
+                const double eq = nb.E[d * P + q];
+                if (eq > emax) {
+                    emax = eq;
+                    ci = q;
+                }
+            }
+        }
+        s_ci = ci;
+    }
+    __syncthreads();
+    const bool climbing = (k == s_ci);
+    // improved tangent: weights of (m+ - m) and (m - m-) from the neighbours' energies
+    float cp = 1.f, cm = 0.f;
+    double inv_t = 0.0, s_ft = 0.0, spring_term = 0.0;
+    if (!end) {
+        const double Em = nb.E[b - 1], E0 = nb.E[b], Ep = nb.E[b + 1];
+        if (Ep > E0 && E0 > Em) {
+            cp = 1.f;
+            cm = 0.f;
+        } else if (Ep < E0 && E0 < Em) {
+            cp = 0.f;
+            cm = 1.f;
+        } else {
+            const double dmax = fmax(fabs(Ep - E0), fabs(Em - E0)), dmin = fmin(fabs(Ep - E0), fabs(Em - E0));
+            cp = (float)(Ep > Em ? dmax : dmin);
+            cm = (float)(Ep > Em ? dmin : dmax);
+        }
+        // pass 1: |t|^2, <g, t>, |m+ - m|^2, |m - m-|^2
+        double stt = 0.0, sft = 0.0, dn = 0.0, dp = 0.0;
+        for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+            const float w = __ldg(&a.node_pos[i].w);
+            const float3 m0 = load_state(nb.m_in, base, np, i);
+            const float3 mp = load_state(nb.m_in, base + S, np, i);
+            const float3 mm = load_state(nb.m_in, base - S, np, i);
+            const float3 dplus = sub3(mp, m0), dminus = sub3(m0, mm);
+            const float3 t = perp3(cp * dplus + cm * dminus, m0);
+            const float3 g = (__ldg(&a.node_mat[i].y) * msc) * perp3(load_state(nb.Bt, base, np, i), m0);
+            stt += (double)(w * dot3(t, t));
+            sft += (double)(w * dot3(g, t));
+            dn += (double)(w * dot3(dplus, dplus));
+            dp += (double)(w * dot3(dminus, dminus));
+        }
+        stt = block_sum_d<kStepThreads>(stt, red);
+        sft = block_sum_d<kStepThreads>(sft, red);
+        dn = block_sum_d<kStepThreads>(dn, red);
+        dp = block_sum_d<kStepThreads>(dp, red);
+        inv_t = stt > 0.0 ? 1.0 / sqrt(stt) : 0.0;
+        s_ft = sft * inv_t;                                  // <g, t_hat>
+        spring_term = (double)nb.spring * (sqrt(dn) - sqrt(dp));
+    }
+    // pass 2: band force and the normalised step
+    const float c_t = climbing ? (float)(-2.0 * s_ft * inv_t) : (float)((spring_term - s_ft) * inv_t);
+    float fmax_loc = 0.f;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        const float3 m0 = load_state(nb.m_in, base, np, i);
+        const float msn = __ldg(&a.node_mat[i].y) * msc;
+        float3 f = msn * perp3(load_state(nb.Bt, base, np, i), m0);
+        if (!end) {
+            const float3 mp = load_state(nb.m_in, base + S, np, i);
+            const float3 mm = load_state(nb.m_in, base - S, np, i);
+            const float3 t = perp3(cp * sub3(mp, m0) + cm * sub3(m0, mm), m0);
+            f = f + c_t * t;
+        }
+        fmax_loc = fmaxf(fmax_loc, sqrtf(dot3(f, f)));
+        const float3 v = normalize3(m0 + nb.step * f);
+        nb.m_out[base + i] = v.x;
+        nb.m_out[base + np + i] = v.y;
+        nb.m_out[base + 2 * np + i] = v.z;
+        write_gemm_input(a, b, i, v, msn);
+    }
+    for (int o = 16; o > 0; o >>= 1) fmax_loc = fmaxf(fmax_loc, __shfl_xor_sync(0xffffffffu, fmax_loc, o));
+    __shared__ float redf[kStepThreads / 32];
+    if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = fmax_loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float f = 0.f;
+        for (int w = 0; w < kStepThreads / 32; ++w) f = fmaxf(f, redf[w]);
+        nb.fmax[b] = f;
+    }
+}
+
+// initial band: m given (rows of [3][n_pad]) or the great circle +z -> -z through +x;
+// writes the GEMM operand of every image
+__global__ void __launch_bounds__(kStepThreads) k_neb_init(StepArgs a, int P, int great_circle) {
+    const int b = blockIdx.x, k = b % P;
+    const int np = a.n_pad;
+    const size_t base = (size_t)b * 3 * np;
+    const float msc = a.isl[3 * b].z;
+    const float th = 3.14159265358979f * (float)k / (float)(P - 1);
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        float3 v;
+        if (great_circle) {
+            v = f3(sinf(th), 0.f, cosf(th));
+            a.m[base + i] = v.x;
+            a.m[base + np + i] = v.y;
+            a.m[base + 2 * np + i] = v.z;
+        } else {
+            v = normalize3(load_state(a.m, base, np, i));
+        }
+        write_gemm_input(a, b, i, v, __ldg(&a.node_mat[i].y) * msc);
+    }
+}
+
 __global__ void __launch_bounds__(kStepThreads) k_init(StepArgs a) {
     __shared__ float red[kStepThreads / 32];
     const int b = blockIdx.x;
@@ -519,6 +695,7 @@ int configure_step_kernels() {
     BPM_CK(cudaFuncSetAttribute(k_stage2<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage2<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_neb_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage1_groups<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage1_groups<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage1_groups<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -603,5 +780,15 @@ void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaSt
     k_field<<<a.B, kStepThreads, stage_smem_bytes(a), s>>>(a, t, mask, out);
 }
 void launch_interval_tick(long long* interval, cudaStream_t s) { k_tick<<<1, 1, 0, s>>>(interval); }
+
+void launch_neb_init(const StepArgs& a, int P, int great_circle, cudaStream_t s) {
+    k_neb_init<<<a.B, kStepThreads, 0, s>>>(a, P, great_circle);
+}
+void launch_neb_energy(const StepArgs& a, float* Bt, double* E, double vol_scale, cudaStream_t s) {
+    k_neb_energy<<<a.B, kStepThreads, stage_smem_bytes(a), s>>>(a, Bt, E, vol_scale);
+}
+void launch_neb_step(const StepArgs& a, const NebArgs& nb, cudaStream_t s) {
+    k_neb_step<<<a.B, kStepThreads, 0, s>>>(a, nb);
+}
 
 }  // namespace bpm

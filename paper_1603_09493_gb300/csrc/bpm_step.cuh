@@ -67,6 +67,22 @@ int stage_islands_per_cta(const StepArgs& a);
 void launch_init(const StepArgs& a, cudaStream_t s);
 void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaStream_t s);
 void launch_interval_tick(long long* interval, cudaStream_t s);
+
+// nudged elastic band (rows of a.m are images; a.x0 is the frozen head position)
+struct NebArgs {
+    int P;                    // images per band (rows d * P .. d * P + P - 1)
+    int climb;                // 1: the highest interior image of each band climbs
+    float step;               // m <- N(m + step * force), force in MA/m x T
+    float spring;             // spring constant, MA/m x T per unit of weighted distance
+    const double* E;          // [rows] energies of m_in (J)
+    const float* Bt;          // [rows][3][n_pad] effective field of m_in (T)
+    const float* m_in;        // [rows][3][n_pad]
+    float* m_out;             // [rows][3][n_pad]
+    float* fmax;              // [rows] max_i |band force_i| of this update
+};
+void launch_neb_init(const StepArgs& a, int P, int great_circle, cudaStream_t s);
+void launch_neb_energy(const StepArgs& a, float* Bt, double* E, double vol_scale, cudaStream_t s);
+void launch_neb_step(const StepArgs& a, const NebArgs& nb, cudaStream_t s);
 int configure_step_kernels();
 
 }  // namespace bpm
