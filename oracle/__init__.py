@@ -18,6 +18,7 @@ Modules
   ber       bit-error-rate formulas of Sec. II.C (Eqs. 1-3)
   hcrit     critical-field search of Sec. II.C
   neb       nudged elastic band for the adjacent-track barrier (Sec. II.C, Eq. 3)
+  ego       efficient global optimisation: maximin Latin hypercube, kriging, EI (Sec. II.A)
 
 Parity status: the full switching dynamics of an island is pinned only
 through its invariants and closed-form special cases (no trajectory is printed

@@ -482,3 +482,39 @@ def screening_designs(N: int, seed: int, mesh_id: int = 0, first_index: int = 0)
     X = np.zeros((N, 16), np.float32)
     X[:, :len(keys)] = 2.0 * U - 1.0
     return isl, X
+
+
+# --------------------------------------------------------------------------
+# random inputs of the global optimiser (Latin hypercubes, candidate points)
+# --------------------------------------------------------------------------
+def lhs_candidates(T: int, n: int, d: int, seed: int) -> np.ndarray:
+    """T random Latin hypercubes of n points in [0, 1)^d, [T][n][d]: in every
+    column the points fall one per stratum [j/n, (j+1)/n), each at a uniform
+    offset inside its stratum."""
+    out = np.empty((T, n, d))
+    for t in range(T):
+        for k in range(d):
+            base = (t * d + k) * n
+            perm = np.argsort(counter_uniform(seed, 300, np.arange(base, base + n)), kind="stable")
+            off = counter_uniform(seed, 301, np.arange(base, base + n))
+            out[t, :, k] = (perm + off) / n
+    return out
+
+
+def unit_points(N: int, d: int, seed: int, stream: int) -> np.ndarray:
+    """N uniform points in (0, 1)^d, [N][d]."""
+    return counter_uniform(seed, 400 + stream, np.arange(N * d)).reshape(N, d)
+
+
+def theta_unit_draws(T: int, d: int, seed: int, round_: int) -> np.ndarray:
+    """Unit uniforms [T][d] for round `round_` of the correlation-length search."""
+    return counter_uniform(seed, 500 + round_, np.arange(T * d)).reshape(T, d)
+
+
+def branin01(X: np.ndarray) -> np.ndarray:
+    """Branin's test function on [0,1]^2 (x1 in [-5, 10], x2 in [0, 15]); global
+    minimum 0.397887 at three points."""
+    x1 = -5.0 + 15.0 * X[:, 0]
+    x2 = 15.0 * X[:, 1]
+    a, b, c, r, s, t = 1.0, 5.1 / (4 * math.pi ** 2), 5.0 / math.pi, 6.0, 10.0, 1.0 / (8 * math.pi)
+    return a * (x2 - b * x1 ** 2 + c * x1 - r) ** 2 + s * (1 - t) * np.cos(x1) + s
