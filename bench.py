@@ -196,6 +196,28 @@ def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400):
                     "wall-clock incl. buffer setup and convergence checks every 50 updates"}
 
 
+def measure_ego(ctx, n=240, d=12, T=256, N=1 << 20):
+    """EGO steps on the GPU (Sec. II.A) at the paper's scale of ten or more training
+    designs per parameter: a batch of T likelihood evaluations (one Cholesky each)
+    and the expected improvement at N candidates; wall-clock of each call."""
+    from paper_1603_09493_gb300 import ego, synth
+    X = synth.unit_points(n, d, 12, 0)
+    y = np.sin(3.0 * X).sum(1)
+    th = 10.0 ** (0.5 + synth.theta_unit_draws(T, d, 12, 0))
+    ego.nll(ctx, X, y, th[:8])                                                 # warm-up
+    t = time.perf_counter()
+    v = ego.nll(ctx, X, y, th)
+    t_nll = time.perf_counter() - t
+    C = synth.unit_points(N, d, 12, 1)
+    with ego.Kriging(ctx, X, y, th[int(np.argmin(v))]) as gp:
+        gp.predict(C[:4096], float(y.min()))
+        t = time.perf_counter()
+        gp.predict(C, float(y.min()))
+        t_ei = time.perf_counter() - t
+    return {"nll_evals_per_s": T / t_nll, "ei_candidates_per_s": N / t_ei, "train_designs": n, "params": d,
+            "theta_batch": T, "candidates": N, "note": "FP64; wall-clock per library call incl. host<->device copies"}
+
+
 def measure_surrogate(ctx, torch, stream, n_infer=16384, n_train=65536, batch=4096, reps=20):
     """Surrogate MLP 16-256x4-2 (BF16 tensor-core GEMMs): inference evals/s on a
     device-resident screening batch, training samples/s (AdamW steps)."""
@@ -450,6 +472,7 @@ def main(args):
         extras["plain"] = measure_plain(ctx, isl, p, hid, prec, n)
         extras["surrogate"] = measure_surrogate(ctx, torch, stream)
         extras["neb"] = measure_neb(ctx, mid, hm, hid)
+        extras["ego"] = measure_ego(ctx)
     ctx.close()
     if rank != 0:
         return 0

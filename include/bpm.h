@@ -410,6 +410,47 @@ int bpm_neb_run(bpm_ctx* ctx, const bpm_island* isl, int32_t D, const bpm_neb_pa
                 int32_t ld, double* E_path, double* E_barrier, float* m_path, int32_t* iters_done,
                 double* max_force);
 
+/* ---------------------------------------------------------------------- */
+/* Efficient global optimisation (Sec. II.A; Jones et al. 1998)            */
+/* ---------------------------------------------------------------------- */
+
+/* The paper's optimiser fills the design space with an optimised Latin
+ * hypercube (at least ten designs per parameter), describes the evaluated
+ * designs with a Gaussian process, and evaluates the design of highest
+ * expected improvement next, refitting after every evaluation.  Kriging model
+ * on the unit cube (FP64 throughout):
+ *   R_ij = exp(-sum_k theta_k (x_ik - x_jk)^2) + nugget [i == j]
+ *   mu = 1'R^-1 y / 1'R^-1 1,  sigma2 = (y - mu 1)'R^-1(y - mu 1) / n
+ *   nll(theta) = n ln sigma2 + ln det R   (concentrated negative log-likelihood)
+ *   yhat(x) = mu + r'R^-1(y - mu 1),
+ *   s2(x) = sigma2 [1 - r'R^-1 r + (1 - 1'R^-1 r)^2 / 1'R^-1 1],  r_i = R(x, x_i)
+ *   EI(x) = (f_min - yhat) Phi(z) + s phi(z),  z = (f_min - yhat) / s  (f_min - yhat clipped at 0 when s = 0)
+ * Limits: 2 <= n <= 2048 training designs, 1 <= d <= 64 parameters. */
+
+/* Maximin choice among T candidate designs cands [T][n][d] (host): *best = the
+ * index whose smallest squared pairwise distance is largest; min_d2 [T]
+ * (nullable) receives every candidate's smallest squared distance. */
+int bpm_lhs_maximin(bpm_ctx* ctx, const double* cands, int32_t T, int32_t n, int32_t d, int32_t* best,
+                    double* min_d2);
+
+/* nll for T correlation vectors theta [T][d] (host; theta_k > 0) on the data
+ * X [n][d], y [n] (host); nll [T] receives +inf where R is not positive
+ * definite.  One CTA factors one matrix; all T in one launch. */
+int bpm_gp_nll(bpm_ctx* ctx, const double* X, const double* y, int32_t n, int32_t d, const double* theta,
+               int32_t T, double nugget, double* nll);
+
+/* Fit the kriging model at theta [d]: factor, inverse factor and weights stay
+ * on the device under *gp_id; mu_sigma2 [2] (nullable) receives mu and sigma2.
+ * BPM_ERR_NONFINITE if R is not positive definite. */
+int bpm_gp_create(bpm_ctx* ctx, const double* X, const double* y, int32_t n, int32_t d, const double* theta,
+                  double nugget, int32_t* gp_id, double* mu_sigma2);
+
+/* yhat, s and EI below f_min at N candidates C [N][d] (host); each output
+ * [N] host and nullable.  Processed in chunks of 32768 candidates. */
+int bpm_gp_predict(bpm_ctx* ctx, int32_t gp_id, const double* C, int64_t N, double f_min, double* yhat,
+                   double* s, double* ei);
+int bpm_gp_destroy(bpm_ctx* ctx, int32_t gp_id);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,12 @@ PROTOTYPES = {
     "bpm_batch_graph_kernels": (c_int, [c_void_p, POINTER(c_int32)]),
     "bpm_neb_run": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_neb_params), c_void_p, c_int32, c_void_p,
                             c_void_p, c_void_p, POINTER(c_int32), POINTER(c_double)]),
+    "bpm_lhs_maximin": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_int32, POINTER(c_int32), c_void_p]),
+    "bpm_gp_nll": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32, c_double, c_void_p]),
+    "bpm_gp_create": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_double, POINTER(c_int32),
+                              c_void_p]),
+    "bpm_gp_predict": (c_int, [c_void_p, c_int32, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p]),
+    "bpm_gp_destroy": (c_int, [c_void_p, c_int32]),
     "bpm_batch_time": (c_int, [c_void_p, POINTER(c_double)]),
     "bpm_batch_destroy": (c_int, [c_void_p]),
     "bpm_run_batch": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,

@@ -316,6 +316,7 @@ void bpm_destroy(bpm_ctx* ctx) {
     live_batches(ctx).clear();
     for (Mesh* m : ctx->meshes) free_mesh(m);
     for (Mlp* m : ctx->mlps) free_mlp(m);
+    for (Gp* g : ctx->gps) free_gp(g);
     for (HeadMap* h : ctx->maps) {
         if (h) {
             if (h->tex) cudaDestroyTextureObject(h->tex);

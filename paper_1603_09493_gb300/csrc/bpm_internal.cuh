@@ -78,6 +78,8 @@ struct HeadMap {
 
 struct Mlp;
 void free_mlp(Mlp* m);
+struct Gp;
+void free_gp(Gp* g);
 
 }  // namespace bpm
 
@@ -90,6 +92,7 @@ struct bpm_ctx {
     std::vector<bpm::Mesh*> meshes;
     std::vector<bpm::HeadMap*> maps;
     std::vector<bpm::Mlp*> mlps;
+    std::vector<bpm::Gp*> gps;
 };
 
 namespace bpm {
