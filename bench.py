@@ -262,8 +262,9 @@ def main_reference(args):
     isl = synth.jittered_islands(8, seed=1)
     ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
     pp = type(p)(**{**p.__dict__})
+    # the step count of the whole workload (the field bound over all its islands), as the GPU arm uses
+    k = llg.stable_substeps(llg.Batch(ops, synth.jittered_islands(B_ISLANDS, seed=1), pp, head_map=hm))
     bt = llg.Batch(ops, isl, pp, head_map=hm)
-    k = llg.stable_substeps(bt)
     pp.substeps = k
     pp.t_end_ps = DT_PS
     for _ in range(args.warmup):
@@ -291,7 +292,8 @@ def main_reference(args):
 def main_uneven(args):
     """The uneven workload: 16 design variants (518-3906 nodes), each with
     `realisations` jittered targets plus two adjacent-track islands (staggered
-    layout), all in one batch (one graph, groups forked over streams)."""
+    layout), all in one batch (one graph: a grouped demag GEMM over all mesh
+    groups and one stage launch per occupancy class per Heun stage)."""
     import torch
     from paper_1603_09493_gb300 import _lib as L
     from paper_1603_09493_gb300 import api, synth
