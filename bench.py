@@ -130,10 +130,22 @@ def gemm_traffic(prec, B, n):
     return NCU_GEMM_TRAFFIC.get((int(prec), int(B), int(n)))
 
 
+_ORACLE_OPS = {}
+
+
+def oracle_ops(mesh, mats):
+    """The oracle's operators of a mesh, built once per run (about a minute for the census mesh)."""
+    from oracle import fem
+    key = (id(mesh), id(mats))
+    if key not in _ORACLE_OPS:
+        _ORACLE_OPS[key] = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    return _ORACLE_OPS[key]
+
+
 def run_oracle_sample(islands, n_intervals, k, mesh, mats, hm, p):
     """Time the FP64 oracle on a bounded sample; returns seconds."""
-    from oracle import fem, llg
-    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    from oracle import llg
+    ops = oracle_ops(mesh, mats)
     pp = type(p)(**{**p.__dict__})
     pp.substeps = k
     pp.t_end_ps = pp.t0_ps + n_intervals * pp.dt_ps
@@ -173,7 +185,7 @@ def measure_plain(ctx, isl, p, hid, prec, n, islands=8, intervals=2):
             "same_switch_flags": bool(np.array_equal(plain["switched"], mixed["switched"]))}
 
 
-def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400):
+def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400, mesh=None, mats=None):
     """Adjacent-track barriers (Sec. II.C, Eq. 3): D islands of the census mesh on
     the adjacent track (12.7 nm cross-track), head frozen 2 nm into the map, one
     band of P images each, BF16x3 demag; wall-clock of the bpm_neb_run call."""
@@ -188,7 +200,18 @@ def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400):
                             map_id=hid, head_map=hm)
     wall = time.perf_counter() - t
     kt = out["E_B_kT"]
+    oracle = None
+    if mesh is not None:
+        # the FP64 oracle band on one band of the same workload, two updates
+        from oracle import neb as oneb
+        ops = oracle_ops(mesh, mats)
+        t = time.perf_counter()
+        oneb.island_band(ops, isl.subset(np.arange(1)), p, hm, oneb.great_circle_path(ops.n, P)[None], 2, step, 1.0)
+        to = time.perf_counter() - t
+        oracle = {"value": P * 2 / to, "unit": "band-image updates/s", "kind": "oracle",
+                  "cores": len(os.sched_getaffinity(0)), "sample": f"1 band x {P} images x 2 updates, {to:.1f} s"}
     return {"image_updates_per_s": D * P * out["iters"] / wall, "unit": "band-image updates/s", "bands": D,
+            "cpu_baseline": oracle,
             "images": P, "iters": out["iters"], "wall_s": wall, "max_force": out["max_force"],
             "E_B_kT_median": float(np.median(kt)), "E_B_kT_min": float(np.min(kt)),
             "ber_adj_median": float(np.median(out["ber_adj"])),
@@ -214,8 +237,21 @@ def measure_ego(ctx, n=240, d=12, T=256, N=1 << 20):
         t = time.perf_counter()
         gp.predict(C, float(y.min()))
         t_ei = time.perf_counter() - t
+    # the FP64 oracle on bounded samples of the same calls
+    from oracle import ego as oego
+    t = time.perf_counter()
+    for q in range(16):
+        oego.nll(X, y, th[q])
+    o_nll = 16 / (time.perf_counter() - t)
+    gpo = oego.fit(X, y, th[int(np.argmin(v))])
+    t = time.perf_counter()
+    oego.predict(gpo, C[:16384], float(y.min()))
+    o_ei = 16384 / (time.perf_counter() - t)
     return {"nll_evals_per_s": T / t_nll, "ei_candidates_per_s": N / t_ei, "train_designs": n, "params": d,
-            "theta_batch": T, "candidates": N, "note": "FP64; wall-clock per library call incl. host<->device copies"}
+            "theta_batch": T, "candidates": N, "note": "FP64; wall-clock per library call incl. host<->device copies",
+            "cpu_baseline": {"nll_evals_per_s": o_nll, "ei_candidates_per_s": o_ei, "kind": "oracle",
+                             "cores": len(os.sched_getaffinity(0)),
+                             "sample": "16 likelihood evaluations; EI at 16384 candidates (numpy FP64)"}}
 
 
 def measure_surrogate(ctx, torch, stream, n_infer=16384, n_train=65536, batch=4096, reps=20):
@@ -351,11 +387,32 @@ def main_uneven(args):
     return 0
 
 
+def main_extras(args):
+    """The NEXT-row measurements alone (band barriers, EGO steps) on the census
+    mesh, one JSON line; used for their launch lists."""
+    import torch
+    from paper_1603_09493_gb300 import api
+    torch.cuda.set_device(0)
+    ctx = api.Context(0, stream=torch.cuda.Stream())
+    mesh, mats, hm, p = workload()
+    mid = ctx.mesh_upload(mesh, mats)
+    hid = ctx.headmap_upload(hm)
+    line = {"workload": "extras (census mesh)",
+            "neb": measure_neb(ctx, mid, hm, hid, mesh=None if args.no_cpu else mesh,
+                               mats=None if args.no_cpu else mats),
+            "ego": measure_ego(ctx)}
+    ctx.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main(args):
     if args.impl == "reference":
         return main_reference(args)
     if args.workload == "uneven":
         return main_uneven(args)
+    if args.workload == "extras":
+        return main_extras(args)
     import torch
     from paper_1603_09493_gb300 import _lib as L
     from paper_1603_09493_gb300 import api, synth
@@ -473,7 +530,8 @@ def main(args):
     if not args.no_extras and rank == 0:
         extras["plain"] = measure_plain(ctx, isl, p, hid, prec, n)
         extras["surrogate"] = measure_surrogate(ctx, torch, stream)
-        extras["neb"] = measure_neb(ctx, mid, hm, hid)
+        extras["neb"] = measure_neb(ctx, mid, hm, hid, mesh=None if args.no_cpu else mesh,
+                                    mats=None if args.no_cpu else mats)
         extras["ego"] = measure_ego(ctx)
     ctx.close()
     if rank != 0:
@@ -502,6 +560,6 @@ if __name__ == "__main__":
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", default="census", choices=["census", "uneven"])
+    ap.add_argument("--workload", default="census", choices=["census", "uneven", "extras"])
     ap.add_argument("--realisations", type=int, default=512)
     sys.exit(main(ap.parse_args()))
