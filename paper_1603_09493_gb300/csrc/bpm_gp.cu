@@ -234,7 +234,9 @@ __global__ void k_gp_corr(const double* __restrict__ C, const double* __restrict
     Rc[q] = exp(-s);
 }
 
-// V[N][n] = Rc[N][n] * Linv[n][n]^T, FP64, 64 x 64 tiles, 4 x 4 outputs per thread
+// V[N][n] = Rc[N][n] * Linv[n][n]^T, FP64, 64 x 64 tiles, 4 x 4 outputs per thread.  B lower
+// triangular: row r of B is zero past column r, so output columns n0 .. n0 + 63 need K only up
+// to n0 + 64 (the skipped products are exact zeros; the sums are unchanged)
 constexpr int kTM = 64, kTN = 64, kTK = 16;
 __global__ void __launch_bounds__(256) k_gp_gemm_nt(const double* __restrict__ A, const double* __restrict__ B,
                                                     int M, int N, int K, double* __restrict__ Cout) {
@@ -243,7 +245,8 @@ __global__ void __launch_bounds__(256) k_gp_gemm_nt(const double* __restrict__ A
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
     double acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += kTK) {
+    const int kend = min(K, n0 + kTN);
+    for (int k0 = 0; k0 < kend; k0 += kTK) {
         for (int e = threadIdx.x; e < kTM * kTK; e += 256) {
             const int r = e / kTK, kk = e % kTK;
             As[kk][r] = (m0 + r < M && k0 + kk < K) ? A[(size_t)(m0 + r) * K + k0 + kk] : 0.0;
