@@ -201,6 +201,19 @@ int bpm_batch_advance(bpm_batch* bt, int32_t n_intervals);
  * on_device: all outputs are device pointers (no synchronisation). */
 int bpm_batch_read(bpm_batch* bt, float* m, int32_t ld, uint8_t* switched, float* t_sw_ps,
                    int32_t* status, float* mz, int on_device);
+/* Energy and torque check of the current state (the FP64 check of a run's
+ * state; the paper's solver runs at 0 K, so with damping the energy of a static
+ * field problem only decreases, Sec. II.A).  For every island, at the batch's
+ * current time and with its run's term mask:
+ *   E_J[b]          = -sum_i V_i Ms_i (B_quad,i / 2 + B_lin,i) . m_i   (J), with B_quad the
+ *                     exchange, anisotropy and demag fields and B_lin the head and uniform
+ *                     fields; accumulated in FP64
+ *   max_torque_T[b] = max_i |m_i x B_i| (T), nullable
+ * Host arrays [B] in the batch's island order.  Runs one demag product over
+ * the batch (the batch's Hd buffer is recomputed by the next advance) and
+ * synchronises the context stream.  BPM_ERR_TIMEOUT if a tensor-core GEMM
+ * wait timed out. */
+int bpm_batch_energy(bpm_batch* bt, double* E_J, float* max_torque_T);
 /* Effective field B (tesla) of the current state at time t_ps, restricted to
  * term_mask, into B_out [B][3][ld] (host or device per on_device). */
 int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out, int32_t ld,

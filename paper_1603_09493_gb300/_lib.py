@@ -103,6 +103,7 @@ PROTOTYPES = {
                               c_void_p]),
     "bpm_gp_predict": (c_int, [c_void_p, c_int32, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p]),
     "bpm_gp_destroy": (c_int, [c_void_p, c_int32]),
+    "bpm_batch_energy": (c_int, [c_void_p, c_void_p, c_void_p]),
     "bpm_batch_time": (c_int, [c_void_p, POINTER(c_double)]),
     "bpm_batch_destroy": (c_int, [c_void_p]),
     "bpm_run_batch": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,

@@ -295,6 +295,14 @@ class Batch:
         L.check(self.lib.bpm_batch_field(self.h, float(t_ps), int(term_mask), L.ptr(out), self.n, 0))
         return out
 
+    def energy(self):
+        """Energy (J, FP64 accumulation) and largest torque |m x B| (T) of every island
+        at the batch's current time (bpm_batch_energy)."""
+        E = np.zeros(self.B, np.float64)
+        T = np.zeros(self.B, np.float32)
+        L.check(self.lib.bpm_batch_energy(self.h, L.ptr(E), L.ptr(T)))
+        return E, T
+
     def kernel_times(self, reps: int = 10) -> dict:
         g, s1, s2 = c_double(), c_double(), c_double()
         L.check(self.lib.bpm_batch_kernel_times(self.h, int(reps), byref(g), byref(s1), byref(s2)))

@@ -821,6 +821,56 @@ int bpm_batch_read(bpm_batch* bt, float* m, int32_t ld, uint8_t* switched, float
     return BPM_OK;
 }
 
+int bpm_batch_energy(bpm_batch* bt, double* E_J, float* max_torque_T) {
+    if (!bt || !E_J) {
+        set_error("bad energy arguments");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    cudaStream_t s = bt->ctx->stream;
+    const double t = bt->t0 + bt->intervals_done * bt->p.dt_ps;
+    int r = BPM_OK;
+    if (bt->p.term_mask & BPM_TERM_DEMAG) r = run_demag_all(bt, s);   // B_d of the current state
+    for (auto& g : bt->groups) {
+        if (r != BPM_OK) break;
+        double* dE = nullptr;
+        float* dT = nullptr;
+        cudaError_t e = cudaMallocAsync(&dE, g.B * sizeof(double), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(&dT, g.B * sizeof(float), s);
+        if (e != cudaSuccess) {
+            set_error("energy scratch: %s", cudaGetErrorString(e));
+            r = BPM_ERR_OOM;
+        } else {
+            launch_energy(g.args, t, g.mesh->info.volume_nm3 * 1e-21, dE, dT, s);
+            std::vector<double> hE(g.B);
+            std::vector<float> hT(g.B);
+            e = cudaMemcpyAsync(hE.data(), dE, g.B * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hT.data(), dT, g.B * sizeof(float), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                set_error("energy: %s", cudaGetErrorString(e));
+                r = BPM_ERR_CUDA;
+            } else {
+                for (int k = 0; k < g.B; ++k) {
+                    E_J[g.user_idx[k]] = hE[k];
+                    if (max_torque_T) max_torque_T[g.user_idx[k]] = hT[k];
+                }
+            }
+        }
+        if (dE) cudaFreeAsync(dE, s);
+        if (dT) cudaFreeAsync(dT, s);
+    }
+    if (r == BPM_OK) {
+        int herr = 0;
+        BPM_CK(cudaMemcpy(&herr, bt->gemm_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) {
+            set_error("tensor-core GEMM wait timed out (code %d)", herr);
+            r = BPM_ERR_TIMEOUT;
+        }
+    }
+    return r;
+}
+
 int bpm_batch_field(bpm_batch* bt, double t_ps, uint32_t term_mask, float* B_out, int32_t ld, int on_device) {
     if (!bt || !B_out || ld < bt->n_max) {
         set_error("bad field arguments");

@@ -637,6 +637,45 @@ __global__ void __launch_bounds__(kStepThreads) k_neb_init(StepArgs a, int P, in
     }
 }
 
+// energy (J) and largest torque |m_i x B_i| (T) of every island at time t: the check of a
+// run's state, E = -sum_i V_i Ms_i (B_quad,i / 2 + B_lin,i) . m_i with the head field moved
+// and ramped to t (vol_scale = sum V [nm^3] * 1e-21), FP64 accumulation
+__global__ void __launch_bounds__(kStepThreads) k_energy(StepArgs a, double t, double vol_scale,
+                                                         double* __restrict__ E, float* __restrict__ torque) {
+    extern __shared__ float4 smem4[];
+    __shared__ double red[kStepThreads / 32];
+    __shared__ float redf[kStepThreads / 32];
+    float* sm = reinterpret_cast<float*>(smem4);
+    const int b = blockIdx.x;
+    const int np = a.n_pad;
+    const float4 p0 = a.isl[3 * b], p1 = a.isl[3 * b + 1], p2 = a.isl[3 * b + 2];
+    const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
+    const float xh = a.x0 + a.v_nm_ps * (float)t;
+    stage_state(a.m + (size_t)b * 3 * np, sm, np);
+    __syncthreads();
+    double e = 0.0;
+    float tq = 0.f;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        const float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
+        const float3 Bq = eff_field(a, b, i, mi, sm, p0, p1, p2, ramp, xh, a.mask & kQuadTerms);
+        const float3 Bl = eff_field(a, b, i, mi, sm, p0, p1, p2, ramp, xh, a.mask & kLinTerms);
+        const float3 T = cross3(mi, Bq + Bl);
+        tq = fmaxf(tq, sqrtf(dot3(T, T)));
+        const float msn = __ldg(&a.node_mat[i].y) * p0.z;
+        e += (double)(__ldg(&a.node_pos[i].w) * msn) * (double)dot3(0.5f * Bq + Bl, mi);
+    }
+    const double tot = block_sum_d<kStepThreads>(e, red);
+    for (int o = 16; o > 0; o >>= 1) tq = fmaxf(tq, __shfl_xor_sync(0xffffffffu, tq, o));
+    if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = tq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kStepThreads / 32; ++w) m = fmaxf(m, redf[w]);
+        E[b] = -vol_scale * tot;
+        torque[b] = m;
+    }
+}
+
 __global__ void __launch_bounds__(kStepThreads) k_init(StepArgs a) {
     __shared__ float red[kStepThreads / 32];
     const int b = blockIdx.x;
@@ -696,6 +735,7 @@ int configure_step_kernels() {
     BPM_CK(cudaFuncSetAttribute(k_stage2<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_neb_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BPM_CK(cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage1_groups<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage1_groups<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     BPM_CK(cudaFuncSetAttribute(k_stage1_groups<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -781,6 +821,9 @@ void launch_field(const StepArgs& a, double t, unsigned mask, float* out, cudaSt
 }
 void launch_interval_tick(long long* interval, cudaStream_t s) { k_tick<<<1, 1, 0, s>>>(interval); }
 
+void launch_energy(const StepArgs& a, double t, double vol_scale, double* E, float* torque, cudaStream_t s) {
+    k_energy<<<a.B, kStepThreads, stage_smem_bytes(a), s>>>(a, t, vol_scale, E, torque);
+}
 void launch_neb_init(const StepArgs& a, int P, int great_circle, cudaStream_t s) {
     k_neb_init<<<a.B, kStepThreads, 0, s>>>(a, P, great_circle);
 }

@@ -80,6 +80,8 @@ struct NebArgs {
     float* m_out;             // [rows][3][n_pad]
     float* fmax;              // [rows] max_i |band force_i| of this update
 };
+// energy (J) and largest torque |m x B| (T) of each island at time t (a.mask selects the terms)
+void launch_energy(const StepArgs& a, double t, double vol_scale, double* E, float* torque, cudaStream_t s);
 void launch_neb_init(const StepArgs& a, int P, int great_circle, cudaStream_t s);
 void launch_neb_energy(const StepArgs& a, float* Bt, double* E, double vol_scale, cudaStream_t s);
 void launch_neb_step(const StepArgs& a, const NebArgs& nb, cudaStream_t s);
