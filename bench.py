@@ -254,7 +254,7 @@ def measure_ego(ctx, n=240, d=12, T=256, N=1 << 20):
                              "sample": "16 likelihood evaluations; EI at 16384 candidates (numpy FP64)"}}
 
 
-def measure_surrogate(ctx, torch, stream, n_infer=16384, n_train=65536, batch=4096, reps=20):
+def measure_surrogate(ctx, torch, stream, n_infer=262144, n_train=65536, batch=4096, reps=20):
     """Surrogate MLP 16-256x4-2 (BF16 tensor-core GEMMs): inference evals/s on a
     device-resident screening batch, training samples/s (AdamW steps)."""
     from paper_1603_09493_gb300 import synth

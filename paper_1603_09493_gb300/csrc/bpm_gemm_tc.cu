@@ -22,13 +22,20 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 128;
+// warp 0 issues the TMA loads and warp 1 the MMAs; all eight warps run the epilogue, warp w
+// on TMEM lane quarter w % 4 (rows) and column half w / 4
+constexpr int kThreads = 256;
 
-template <int P, int TN>
+// The forward layers of the MLP (bias+GELU and output epilogues) have K <= 256, at most four
+// k-blocks: two stages keep their ring full and halve the shared memory, so that two CTAs share
+// an SM and one CTA's epilogue runs beside the other's MMAs.  The other GEMMs (K = batch rows)
+// keep the deep ring.
+template <int P, int TN, int EPI>
 struct Cfg {
     static constexpr int W_TILE = Tile<TN>::W_TILE;
     static constexpr int stage_bytes = (P == 3 ? 2 : 1) * (A_TILE + W_TILE);
-    static constexpr int stages = (192 * 1024) / stage_bytes;   // 2 (P=3, TN=256) .. 6
+    static constexpr bool forward_layer = EPI == 1 || EPI == 2;   // TC_EPI_BIAS_GELU, TC_EPI_BIAS_OUT
+    static constexpr int stages = forward_layer ? 2 : (192 * 1024) / stage_bytes;   // 2 .. 6
     static constexpr int smem = stages * stage_bytes + 1024 /*align*/ + 256 /*barriers*/;
 };
 
@@ -57,18 +64,29 @@ __device__ __forceinline__ void epilogue32(const TcEpilogue& e, int M, int N, in
                 if (col + q < e.cols_valid) e.C[(size_t)row * e.ldc + col + q] = __uint_as_float(r[q]);
         }
     } else if (EPI == TC_EPI_BIAS_GELU) {
-        // z = acc + b; keep z (for the backward pass) and h = GELU(z) in both layouts
+        // z = acc + b; keep z (for the backward pass, optional) and h = GELU(z) row-major and,
+        // optionally, transposed.  N is a multiple of 32 and the rows of H are 16-byte aligned,
+        // so the 32 columns of h go out as four 16-byte stores.
+        if (col >= N || row >= M) return;
+        uint32_t hp[16];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int c = col + q;
-            if (c >= N) break;
-            const float z = __uint_as_float(r[q]) + (c < e.cols_valid ? e.bias[c] : 0.f);
-            const float h = (c < e.cols_valid) ? gelu(z) : 0.f;
-            // rows past the valid batch are written as zeros so that no stale value travels on
-            if (e.C && rok) e.C[(size_t)row * e.ldc + c] = z;
-            if (row < M) e.H[(size_t)row * e.ldh + c] = __float2bfloat16_rn(rok ? h : 0.f);
-            if (e.HT && row < M) e.HT[(size_t)c * e.ldht + row] = __float2bfloat16_rn(rok ? h : 0.f);
+        for (int q = 0; q < 32; q += 2) {
+            float h2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int c = col + q + u;
+                const float z = __uint_as_float(r[q + u]) + (c < e.cols_valid ? e.bias[c] : 0.f);
+                // rows past the valid batch are written as zeros so that no stale value travels on
+                h2[u] = (rok && c < e.cols_valid) ? gelu(z) : 0.f;
+                if (e.C && rok) e.C[(size_t)row * e.ldc + c] = z;
+                if (e.HT) e.HT[(size_t)c * e.ldht + row] = __float2bfloat16_rn(h2[u]);
+            }
+            const __nv_bfloat162 pk = __floats2bfloat162_rn(h2[0], h2[1]);
+            hp[q / 2] = *reinterpret_cast<const uint32_t*>(&pk);
         }
+        uint4* dst = reinterpret_cast<uint4*>(e.H + (size_t)row * e.ldh + col);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) dst[v] = make_uint4(hp[4 * v], hp[4 * v + 1], hp[4 * v + 2], hp[4 * v + 3]);
     } else if (EPI == TC_EPI_BIAS_OUT) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -98,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
               const __grid_constant__ CUtensorMap mWhi, const __grid_constant__ CUtensorMap mWlo, int M, int N, int K,
               const TcEpilogue e, int* err) {
-    using CF = Cfg<P, TN>;
+    using CF = Cfg<P, TN, EPI>;
     constexpr int W_TILE = CF::W_TILE;
     constexpr int S = CF::stages;
     extern __shared__ uint8_t smem_raw[];
@@ -196,10 +214,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     // tcgen05.ld is warp-collective: take the decision once per warp
     const int go = __shfl_sync(0xffffffffu, (have && *(volatile int*)err == 0) ? 1 : 0, 0);
     if (go) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = m0 + quarter * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-        for (int c = 0; c < TN; c += 32) {
+        for (int c = half * (TN / 2); c < (half + 1) * (TN / 2); c += 32) {
             uint32_t r[32];
             float colsum[32];
             tmem_ld32(lane_addr + (uint32_t)c, r);
@@ -212,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float v = colsum[q];
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                     if (lane == q && col + q < N)
-                        e.colsum[(size_t)(blockIdx.y * 4 + warp) * e.ldcs + col + q] = v;
+                        e.colsum[(size_t)(blockIdx.y * 4 + quarter) * e.ldcs + col + q] = v;
                 }
             }
         }
@@ -231,7 +250,7 @@ int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const 
     static bool configured = false;
     if (!configured) {
         BPM_CK(cudaFuncSetAttribute(k_gemm_tc<P, EPI, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    Cfg<P, TN>::smem));
+                                    Cfg<P, TN, EPI>::smem));
         configured = true;
     }
     CUtensorMap mAhi, mAlo, mWhi, mWlo;
@@ -245,7 +264,7 @@ int launch(cudaStream_t s, int M, int N, int K, const __nv_bfloat16* Ahi, const 
         mWlo = mWhi;
     }
     dim3 grid((N + TN - 1) / TN, M / TM);
-    k_gemm_tc<P, EPI, TN><<<grid, kThreads, Cfg<P, TN>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, e, err);
+    k_gemm_tc<P, EPI, TN><<<grid, kThreads, Cfg<P, TN, EPI>::smem, s>>>(mAhi, mAlo, mWhi, mWlo, M, N, K, e, err);
     BPM_CK(cudaGetLastError());
     return BPM_OK;
 }

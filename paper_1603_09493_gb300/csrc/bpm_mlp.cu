@@ -100,16 +100,34 @@ int ensure_ws(Mlp* m, int rows) {
 }
 
 // rows [0, nb) of X (fp32 [*][n_in]) -> bf16 [rows][in_pad] and its transpose; pads zero
+// the input batch as BF16 [rows][in_pad] (zero padded): one thread per 8 columns of a row, so
+// that a warp writes consecutive 16-byte chunks
 __global__ void k_load_x(int nb, int rows, int n_in, int in_pad, const float* __restrict__ X,
-                         __nv_bfloat16* __restrict__ H0, __nv_bfloat16* __restrict__ H0T) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    for (int c = 0; c < in_pad; ++c) {
-        float v = (r < nb && c < n_in) ? X[(size_t)r * n_in + c] : 0.f;
-        __nv_bfloat16 b = __float2bfloat16_rn(v);
-        H0[(size_t)r * in_pad + c] = b;
-        H0T[(size_t)c * rows + r] = b;
+                         __nv_bfloat16* __restrict__ H0) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunks = in_pad / 8;
+    if (q >= (long long)rows * chunks) return;
+    const int r = (int)(q / chunks), c0 = (int)(q % chunks) * 8;
+    uint32_t pk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 2 * u;
+        const float a = (r < nb && c < n_in) ? X[(size_t)r * n_in + c] : 0.f;
+        const float b = (r < nb && c + 1 < n_in) ? X[(size_t)r * n_in + c + 1] : 0.f;
+        const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        pk[u] = *reinterpret_cast<const uint32_t*>(&v);
     }
+    *reinterpret_cast<uint4*>(H0 + (size_t)r * in_pad + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+}
+
+// its transpose [in_pad][rows] for the weight gradient of the first layer (training only)
+__global__ void k_load_xt(int nb, int rows, int n_in, int in_pad, const float* __restrict__ X,
+                          __nv_bfloat16* __restrict__ H0T) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)rows * in_pad) return;
+    const int c = (int)(q / rows), r = (int)(q % rows);
+    const float v = (r < nb && c < n_in) ? X[(size_t)r * n_in + c] : 0.f;
+    H0T[q] = __float2bfloat16_rn(v);
 }
 
 // loss head (one CTA): mean sigmoid-BCE over nb x n_out, dz = (sigmoid(z) - y) / (nb n_out)
@@ -240,11 +258,12 @@ int forward(Mlp* m, cudaStream_t s, int rows, int nb, bool probs) {
         e.rows_valid = nb;
         e.cols_valid = m->out_real[l];
         if (l < m->L - 1) {
-            e.C = m->Z[l];
+            // the pre-activation z and the transposed activations serve the backward pass only
+            e.C = probs ? nullptr : m->Z[l];
             e.ldc = m->out_pad[l];
             e.H = m->H[l + 1];
             e.ldh = m->in_pad[l + 1];
-            e.HT = m->HT[l + 1];
+            e.HT = probs ? nullptr : m->HT[l + 1];
             e.ldht = rows;
             BPM_TRY(gemm_tc(s, TC_EPI_BIAS_GELU, rows, m->out_pad[l], m->in_pad[l], m->H[l], m->W[l], e, m->err));
         } else {
@@ -433,7 +452,9 @@ int bpm_surrogate_get_params(bpm_ctx* ctx, int32_t sid, float* out) {
 static int load_batch(bpm_ctx* ctx, Mlp* m, const float* Xd, const float* Yd, int nb, int rows) {
     cudaStream_t s = ctx->stream;
     BPM_TRY(ensure_ws(m, rows));
-    k_load_x<<<(rows + 127) / 128, 128, 0, s>>>(nb, rows, m->n_in, m->in_pad[0], Xd, m->H[0], m->HT[0]);
+    const long long cx = (long long)rows * (m->in_pad[0] / 8), ct = (long long)rows * m->in_pad[0];
+    k_load_x<<<(unsigned)((cx + 255) / 256), 256, 0, s>>>(nb, rows, m->n_in, m->in_pad[0], Xd, m->H[0]);
+    if (Yd) k_load_xt<<<(unsigned)((ct + 255) / 256), 256, 0, s>>>(nb, rows, m->n_in, m->in_pad[0], Xd, m->HT[0]);
     BPM_CK(cudaGetLastError());
     if (Yd) {
         BPM_CK(cudaMemsetAsync(m->Y, 0, sizeof(float) * (size_t)rows * m->n_out, s));
@@ -541,7 +562,7 @@ int bpm_surrogate_infer(bpm_ctx* ctx, int32_t sid, const float* X, int64_t N, fl
     }
     BPM_CK(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
-    const int chunk = 16384;
+    const int chunk = 65536;   // 512 row tiles per layer GEMM: enough CTAs for every SM
     const float* Xd = X;
     float* Xtmp = nullptr;
     if (!on_device) {
