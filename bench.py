@@ -406,9 +406,25 @@ def main_extras(args):
     return 0
 
 
+def main_surrogate(args):
+    """The surrogate measurement alone (inference and training), one JSON line; used for its
+    launch list."""
+    import torch
+    from paper_1603_09493_gb300 import api
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = api.Context(0, stream=stream)
+    line = {"workload": "surrogate MLP 16-256x4-2", "surrogate": measure_surrogate(ctx, torch, stream)}
+    ctx.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main(args):
     if args.impl == "reference":
         return main_reference(args)
+    if args.workload == "surrogate":
+        return main_surrogate(args)
     if args.workload == "uneven":
         return main_uneven(args)
     if args.workload == "extras":
@@ -560,6 +576,6 @@ if __name__ == "__main__":
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", default="census", choices=["census", "uneven", "extras"])
+    ap.add_argument("--workload", default="census", choices=["census", "uneven", "extras", "surrogate"])
     ap.add_argument("--realisations", type=int, default=512)
     sys.exit(main(ap.parse_args()))
