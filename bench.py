@@ -110,7 +110,7 @@ def gemm_peak(pk):
     region, same stream and launch configuration), a kernel timed alone at the
     clocks of the run (2.0-2.07 GHz), so the burst cuBLAS figure applies; the
     sustained one was taken over seconds of back-to-back GEMMs at a median SM
-    clock of 1455 MHz."""
+    clock of about 1.5 GHz."""
     if pk:
         return pk["bf16_tflops"], "MEASURED_PEAKS bf16_tflops (burst; kernel timed launch by launch)"
     return 1900.0, "fallback (1.9 PFLOP/s bf16 burst)"
