@@ -151,7 +151,7 @@ const char* bpm_version(void);
  *   tets       [n_tets][4]  host, node indices, any orientation
  *   tet_region [n_tets]     host, index into mats
  *   mats       [n_regions]  host
- * Errors: BPM_ERR_ARG (bad index, degenerate tet, n_nodes > 16384),
+ * Errors: BPM_ERR_ARG (bad index, degenerate tet, n_nodes > 8192),
  *         BPM_ERR_UNSTABLE (CG not converged), BPM_ERR_OOM, BPM_ERR_CUDA. */
 int bpm_mesh_upload(bpm_ctx* ctx, const double* xyz_nm, int32_t n_nodes,
                     const int32_t* tets, int32_t n_tets, const int32_t* tet_region,

@@ -10,6 +10,8 @@ import numpy as np
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libbpmllg.so")
 
 BPM_OK = 0
+BPM_ERR_ARG, BPM_ERR_CUDA, BPM_ERR_OOM, BPM_ERR_TIMEOUT, BPM_ERR_NONFINITE, BPM_ERR_UNSTABLE, BPM_ERR_STATE = \
+    -1, -2, -3, -4, -5, -6, -7
 ERRORS = {-1: "BPM_ERR_ARG", -2: "BPM_ERR_CUDA", -3: "BPM_ERR_OOM", -4: "BPM_ERR_TIMEOUT",
           -5: "BPM_ERR_NONFINITE", -6: "BPM_ERR_UNSTABLE", -7: "BPM_ERR_STATE"}
 

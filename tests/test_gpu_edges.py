@@ -1,0 +1,116 @@
+"""Edge cases of the batched path: an empty batch, a single island (one valid
+row of a 128-row GEMM tile) against the FP64 oracle, and the largest mesh the
+library accepts (8192 nodes).
+
+For the largest mesh the oracle's dense demag assembly (a 24000-unknown LU)
+is out of reach, so the check there covers the assembly residuals, the
+exchange, anisotropy and head terms against the oracle without its demag,
+finite unit-norm states after a few intervals with every term on, and the
+rejection of one node more than the limit."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fem, llg
+from paper_1603_09493_gb300 import _lib as L
+from paper_1603_09493_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not os.path.exists(L.LIB_PATH):
+        from paper_1603_09493_gb300 import build
+        build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def test_empty_batch_is_rejected(ctx):
+    # through the C ABI directly: a batch of zero islands is an argument error
+    from ctypes import byref, c_void_p
+    ctx.mesh_upload(synth.small_island_mesh(), synth.ecc_materials())
+    q = api.run_params(synth.RunParams(dt_ps=0.1, substeps=2))
+    h = c_void_p()
+    assert ctx.lib.bpm_batch_create(ctx.h, None, 0, byref(q), byref(h)) == L.BPM_ERR_ARG
+    assert not h.value
+    assert ctx.lib.bpm_run_batch(ctx.h, None, 0, byref(q), 1, None, 0, None, None, None) == L.BPM_ERR_ARG
+
+
+def test_single_island_matches_oracle(ctx):
+    mesh = synth.small_island_mesh()
+    mats = synth.ecc_materials()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    mid = ctx.mesh_upload(mesh, mats)
+    hm = synth.synthetic_head_map()
+    hid = ctx.headmap_upload(hm)
+    isl = synth.jittered_islands(1, seed=5, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, t_end_ps=30.0, alpha=0.1, rise_ps=10.0, use_map=True, x0_nm=-2.0,
+                        uniform_T=synth.uniform_field(0.6, 165.0))
+    p.substeps = llg.stable_substeps(llg.Batch(ops, isl, p, head_map=hm))
+    ref = llg.Batch(ops, isl, p, head_map=hm).run()
+    for prec in (L.PREC_FP32, L.PREC_BF16X3):
+        out = ctx.run_batch(isl, p, p.n_intervals, precision=prec, map_id=hid)
+        err = np.abs(out["m"].transpose(0, 2, 1) - ref["m"]).max()
+        print(f"single island, prec {prec}: max |dm| {err:.2e}")
+        assert err <= 1e-3
+        assert np.array_equal(out["switched"], ref["switched"])
+        assert np.all(out["status"] == 0)
+
+
+def _largest_mesh():
+    # 10 hexagonal rings (331 nodes a plane) x 24 planes = 7944 nodes, 20 nm across
+    return synth.layered_island_mesh(20.0, 7.0, 3.0, rings=10, hard_slabs=16, soft_slabs=7, seed=3)
+
+
+def test_largest_mesh(ctx):
+    mesh = _largest_mesh()
+    assert 7900 <= mesh.n_nodes <= 8192
+    mats = synth.ecc_materials()
+    mid = ctx.mesh_upload(mesh, mats)
+    info = ctx.mesh_info(mid)
+    assert info["n_nodes"] == mesh.n_nodes
+    assert info["cg_residual_neumann"] < 1e-12 and info["cg_residual_dirichlet"] < 1e-12
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats, with_demag=False)
+    hm = synth.synthetic_head_map()
+    hid = ctx.headmap_upload(hm)
+    B = 130                                                   # one full and one ragged row tile
+    isl = synth.jittered_islands(B, seed=7, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, substeps=2, alpha=0.1, rise_ps=10.0, use_map=True,
+                        uniform_T=synth.uniform_field(0.5, 160.0))
+    rng = np.random.default_rng(3)
+    m = rng.standard_normal((2, mesh.n_nodes, 3)) * 0.3 + np.array([0.0, 0.0, 1.0])
+    m /= np.linalg.norm(m, axis=-1, keepdims=True)
+    two = isl.subset(np.arange(2))
+    ob = llg.Batch(ops, two, p, head_map=hm)
+    with ctx.batch(two, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+        bt.set_state(m.transpose(0, 2, 1).astype(np.float32), 0.0)
+        mf = bt.read()["m"].transpose(0, 2, 1).astype(np.float64)
+        for term in (L.TERM_EXCHANGE, L.TERM_ANISOTROPY, L.TERM_HEAD):
+            g = bt.field(4.0, term).transpose(0, 2, 1)
+            o = ob.field(mf, 4.0, term)
+            err = np.abs(g - o).max() / max(np.abs(o).max(), 1e-3)
+            print(f"largest mesh, term {term}: rel err {err:.2e}")
+            assert err <= 2e-5
+    # every term on, a ragged batch of 130 islands, a few intervals
+    bound = api.field_bound(ctx, mid, isl, p, hm)
+    p.substeps = api.stable_substeps(bound, p.dt_ps, p.alpha)
+    out = ctx.run_batch(isl, p, 3, precision=L.PREC_BF16X3, map_id=hid)
+    assert np.all(out["status"] == 0)
+    nrm = np.linalg.norm(out["m"][:, :, :mesh.n_nodes], axis=1)
+    assert np.abs(nrm - 1.0).max() < 1e-5
+
+
+def test_one_node_past_the_limit_is_rejected(ctx):
+    mesh = _largest_mesh()
+    n = mesh.n_nodes
+    # append isolated nodes up to 8193 (they belong to no tet): the size check comes first
+    extra = 8193 - n
+    xyz = np.concatenate([mesh.xyz_nm, mesh.xyz_nm[:extra] + np.array([0.0, 0.0, 50.0])])
+    big = synth.IslandMesh(xyz_nm=xyz, tets=mesh.tets, tet_region=mesh.tet_region,
+                           z_interface_nm=mesh.z_interface_nm, height_nm=mesh.height_nm)
+    with pytest.raises(RuntimeError):
+        ctx.mesh_upload(big, synth.ecc_materials())
