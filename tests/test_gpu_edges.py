@@ -114,3 +114,49 @@ def test_one_node_past_the_limit_is_rejected(ctx):
                            z_interface_nm=mesh.z_interface_nm, height_nm=mesh.height_nm)
     with pytest.raises(RuntimeError):
         ctx.mesh_upload(big, synth.ecc_materials())
+
+
+def test_undamped_precession_in_a_uniform_field(ctx):
+    # alpha = 0, a uniform 1 T field along z and no other term: every node precesses about z at
+    # gamma B, m_z stays fixed.  Heun with renormalisation keeps |m| and errs in phase by about
+    # N (omega h)^3 / 6 after N steps (omega h = 0.0088 here).
+    mid = ctx.mesh_upload(synth.small_island_mesh(), synth.ecc_materials())
+    isl = synth.jittered_islands(3, seed=2, mesh_id=mid)
+    isl.Hext_T[:] = 0.0
+    p = synth.RunParams(dt_ps=0.1, substeps=2, alpha=0.0, rise_ps=0.0, use_map=False, term_mask=L.TERM_UNIFORM,
+                        uniform_T=(0.0, 0.0, 1.0))
+    n = ctx.mesh_info(mid)["n_nodes"]
+    th = np.deg2rad(30.0)
+    m0 = np.zeros((3, 3, n), np.float32)
+    m0[:, 0, :], m0[:, 2, :] = np.sin(th), np.cos(th)
+    intervals = 200                                              # 20 ps, 400 Heun steps
+    with ctx.batch(isl, p, precision=L.PREC_FP32) as bt:
+        bt.set_state(m0, 0.0)
+        bt.advance(intervals)
+        m = bt.read()["m"]
+    gamma = 1.76085963023e-1                                      # rad / (ps T)
+    phi = gamma * 1.0 * intervals * p.dt_ps                       # dm/dt = -gamma m x B: phi' = +gamma B
+    ref = np.array([np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi), np.cos(th)])
+    steps = intervals * p.substeps
+    wh = gamma * p.dt_ps / p.substeps
+    tol = steps * wh ** 3 / 6.0 + 1e-4                            # phase error + FP32 rounding over 400 steps
+    err = np.abs(m - ref[None, :, None]).max()
+    print(f"precession: max |dm| {err:.2e}, bound {tol:.2e}")
+    assert err <= tol
+    assert np.abs(m[:, 2, :] - np.cos(th)).max() <= 1e-5
+
+
+def test_no_field_leaves_the_state_unchanged(ctx):
+    mid = ctx.mesh_upload(synth.small_island_mesh(), synth.ecc_materials())
+    isl = synth.jittered_islands(4, seed=3, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, substeps=3, alpha=0.1, use_map=False, term_mask=0)
+    n = ctx.mesh_info(mid)["n_nodes"]
+    rng = np.random.default_rng(9)
+    m0 = rng.standard_normal((4, 3, n))
+    m0 = (m0 / np.linalg.norm(m0, axis=1, keepdims=True)).astype(np.float32)
+    for prec in (L.PREC_FP32, L.PREC_BF16X3):
+        with ctx.batch(isl, p, precision=prec) as bt:
+            bt.set_state(m0, 0.0)
+            bt.advance(10)
+            m = bt.read()["m"]
+        assert np.abs(m - m0).max() <= 1e-6
