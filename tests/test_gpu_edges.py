@@ -160,3 +160,25 @@ def test_no_field_leaves_the_state_unchanged(ctx):
             bt.advance(10)
             m = bt.read()["m"]
         assert np.abs(m - m0).max() <= 1e-6
+
+
+def test_stoner_wohlfarth_switching_field_at_45_degrees(ctx):
+    # a small homogeneous island (5 nm, hard material, no demag) reverses coherently: with the
+    # field at 45 degrees to the easy axis (135 degrees from the initial +z) it switches above
+    # h = B / B_K = 0.5 and stays below, B_K = 2 K / Ms (Stoner-Wohlfarth astroid)
+    mesh = synth.layered_island_mesh(5.0, 4.0, 1.0, rings=2, hard_slabs=4, soft_slabs=1, seed=0)
+    K, Ms = 0.9e6, 0.8e6
+    mats = synth.ecc_materials(Ms_hard=Ms, Ku_hard=K, Ms_soft=Ms, Ku_soft=K, interlayer_scale=1.0)
+    mid = ctx.mesh_upload(mesh, mats)
+    BK = 2.0 * K / Ms
+    hs = [0.47, 0.53]
+    isl = synth.Islands(np.full(2, mid, np.int32), np.ones(2, np.float32), np.ones(2, np.float32),
+                        np.tile(np.array([[0.0, 0.0, 1.0]], np.float32), (2, 1)), np.zeros((2, 2), np.float32),
+                        np.array([[h * BK * np.sin(np.deg2rad(135.0)), 0.0, h * BK * np.cos(np.deg2rad(135.0))]
+                                  for h in hs], np.float32))
+    p = synth.RunParams(dt_ps=1.0, t_end_ps=600.0, alpha=1.0, rise_ps=0.0, use_map=False,
+                        term_mask=L.TERM_EXCHANGE | L.TERM_ANISOTROPY | L.TERM_UNIFORM)
+    p.substeps = api.stable_substeps(api.field_bound(ctx, mid, isl, p), p.dt_ps, p.alpha)
+    out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_FP32)
+    print("switched", out["switched"], "t_sw", out["t_sw"])
+    assert not out["switched"][0] and out["switched"][1]
