@@ -30,6 +30,8 @@ constexpr int kThreads = 256;
 // k-blocks: two stages keep their ring full and halve the shared memory, so that two CTAs share
 // an SM and one CTA's epilogue runs beside the other's MMAs.  The other GEMMs (K = batch rows)
 // keep the deep ring.
+// The forward layers launch 128-wide column tiles: at 64 KB of ring a CTA, three CTAs (24 warps)
+// share an SM for the GELU epilogue, which bounds these layers.
 template <int P, int TN, int EPI>
 struct Cfg {
     static constexpr int W_TILE = Tile<TN>::W_TILE;
@@ -326,8 +328,8 @@ int gemm_tc(cudaStream_t s, int epi, int M, int N, int K, const __nv_bfloat16* A
     }
     switch (epi) {
         case TC_EPI_STORE: return launch<1, TC_EPI_STORE>(s, M, N, K, A, A, W, W, e, err_flag);
-        case TC_EPI_BIAS_GELU: return launch<1, TC_EPI_BIAS_GELU>(s, M, N, K, A, A, W, W, e, err_flag);
-        case TC_EPI_BIAS_OUT: return launch<1, TC_EPI_BIAS_OUT>(s, M, N, K, A, A, W, W, e, err_flag);
+        case TC_EPI_BIAS_GELU: return launch<1, TC_EPI_BIAS_GELU, 128>(s, M, N, K, A, A, W, W, e, err_flag);
+        case TC_EPI_BIAS_OUT: return launch<1, TC_EPI_BIAS_OUT, 128>(s, M, N, K, A, A, W, W, e, err_flag);
         case TC_EPI_GELU_BWD: return launch<1, TC_EPI_GELU_BWD>(s, M, N, K, A, A, W, W, e, err_flag);
         default: set_error("unknown epilogue %d", epi); return BPM_ERR_ARG;
     }
