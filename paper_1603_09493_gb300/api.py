@@ -337,18 +337,26 @@ class Batch:
         import json
         import os
         key = self.tuning_key(device_name)
-        cache = {}
-        if os.path.exists(cache_path):
-            with open(cache_path) as f:
-                cache = json.load(f)
+        def load():
+            try:
+                with open(cache_path) as f:
+                    return json.load(f)
+            except (OSError, ValueError):               # absent, or cut short by another writer
+                return {}
+        cache = load()
         if key in cache:
             self.set_tuning(**cache[key])
             return dict(cache[key], cached=True)
         t = self.autotune(reps)
+        # several processes (one per GPU) may share the file: merge with what is there now and
+        # replace it atomically, so that no reader sees a partial write
+        cache = load()
         cache[key] = t
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
-        with open(cache_path, "w") as f:
+        tmp = f"{cache_path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
         return dict(t, cached=False)
 
     def time(self) -> float:
