@@ -10,6 +10,10 @@ Definitions used (textbook):
   [out][in]; GELU(x) = x * Phi(x) = x/2 (1 + erf(x / sqrt 2));
 * loss = mean over samples and outputs of the sigmoid binary cross-entropy
   with logits: softplus(z) - y z;
+* screened error rates of a design (Sec. II.C: a write error is a target island
+  that fails to switch; an adjacent-track error is a neighbouring island that
+  flips): over the J jittered samples of the design, the mean of
+  P(no switch) = sigmoid(-z_0) and of P(flip) = sigmoid(z_k), k >= 1;
 * AdamW (Loshchilov & Hutter, decoupled weight decay), bias-corrected moments:
       m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
       p -= lr * ( m/(1-b1^t) / (sqrt(v/(1-b2^t)) + eps) + wd * p )
@@ -105,3 +109,25 @@ def train(params, X, Y, epochs, batch, lr, wd, beta1=0.9, beta2=0.999, eps=1e-8)
             grads = backward(params, cache, logits, yb)
             params = adamw_step(params, grads, state, lr, wd, beta1, beta2, eps)
     return params, losses
+
+
+def screened_ber(params, X, n_designs, n_jitter):
+    """Per-design error rates from the surrogate over jitter samples (Sec. II.C).
+
+    X [n_designs * n_jitter][n_in], design-major (rows d*J .. d*J + J - 1 are
+    the jitter samples of design d).  Returns [n_designs][n_out]: column 0 the
+    mean over the samples of the probability that the target island does not
+    switch, sigmoid(-z_0); columns k >= 1 the mean probability of output k,
+    sigmoid(z_k)."""
+    logits, _ = forward(params, X)
+    z = logits.reshape(n_designs, n_jitter, -1).copy()
+    z[:, :, 0] = -z[:, :, 0]
+    return sigmoid_tail(z).mean(axis=1)
+
+
+def sigmoid_tail(z):
+    """1 / (1 + exp(-z)) with full relative precision on both tails: a small
+    probability is exp(z) / (1 + exp(z)), never a difference of values near 1."""
+    z = np.asarray(z, np.float64)
+    e = np.exp(-np.abs(z))
+    return np.where(z >= 0, 1.0 / (1.0 + e), e / (1.0 + e))

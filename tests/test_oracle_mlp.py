@@ -1,5 +1,6 @@
 """Pins of the oracle MLP: finite-difference gradients, GELU/BCE closed forms,
-the closed form of the first AdamW step."""
+the closed form of the first AdamW step, the screened error rates of a
+constant network."""
 import math
 
 import numpy as np
@@ -67,3 +68,38 @@ def test_training_reduces_loss_on_a_separable_task():
     params = _params([16, 32, 32, 2], 4)
     _, losses = mlp.train(params, X, Y, epochs=20, batch=64, lr=3e-3, wd=1e-4)
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_screened_ber_of_a_constant_network():
+    # zero weights: every logit is its bias, so design error rates are closed forms
+    sizes = [16, 8, 2]
+    params = [(np.zeros((o, i)), np.zeros(o)) for i, o in zip(sizes[:-1], sizes[1:])]
+    params[-1] = (np.zeros((2, 8)), np.array([2.0, -3.0]))
+    X = np.random.default_rng(1).uniform(-1, 1, size=(5 * 3, 16))
+    r = mlp.screened_ber(params, X, 5, 3)
+    assert r.shape == (5, 2)
+    assert np.allclose(r[:, 0], 1.0 / (1.0 + math.exp(2.0)), rtol=1e-15, atol=0)     # P(no switch) at z = 2
+    assert np.allclose(r[:, 1], 1.0 / (1.0 + math.exp(3.0)), rtol=1e-15, atol=0)     # P(flip) at z = -3
+    # a far-switching target: the write error rate keeps its relative precision (no 1 - p cancellation)
+    params[-1] = (np.zeros((2, 8)), np.array([40.0, 0.0]))
+    r = mlp.screened_ber(params, X, 5, 3)
+    assert abs(r[0, 0] / math.exp(-40.0) - 1.0) < 1e-12 and r[0, 1] == 0.5
+
+
+def test_screened_ber_is_a_per_design_mean():
+    sizes = [16, 12, 2]
+    params = _params(sizes, 3)
+    D, J = 4, 6
+    X = np.random.default_rng(2).uniform(-1, 1, size=(D * J, 16))
+    r = mlp.screened_ber(params, X, D, J)
+    # brute force, one sample at a time
+    for d in range(D):
+        acc = np.zeros(2)
+        for j in range(J):
+            z, _ = mlp.forward(params, X[d * J + j][None])
+            acc += [1.0 / (1.0 + math.exp(z[0, 0])), 1.0 / (1.0 + math.exp(-z[0, 1]))]
+        assert np.allclose(r[d], acc / J, rtol=1e-13, atol=0)
+    # the order of a design's samples does not matter; designs do not mix
+    perm = np.concatenate([d * J + np.random.default_rng(d).permutation(J) for d in range(D)])
+    assert np.allclose(mlp.screened_ber(params, X[perm], D, J), r, rtol=1e-13, atol=0)
+    assert np.allclose(mlp.screened_ber(params, X[:J], 1, J), r[:1], rtol=1e-15, atol=0)
