@@ -327,6 +327,20 @@ int bpm_surrogate_train(bpm_ctx* ctx, int32_t sid, const float* X, const float* 
 /* Probabilities sigmoid(logits) P [N][n_out] for X [N][n_in] (both host, or both
  * device if on_device, stream-ordered). */
 int bpm_surrogate_infer(bpm_ctx* ctx, int32_t sid, const float* X, int64_t N, float* P, int on_device);
+/* Screened error rates of designs over their jitter samples (Sec. II.C: a write
+ * error is a target island that fails to switch, an adjacent-track error a
+ * neighbouring island that flips).  X [n_designs * n_jitter][n_in] is
+ * design-major: rows d*n_jitter .. d*n_jitter + n_jitter - 1 are the jitter
+ * samples of design d.  rates [n_designs][n_out] (float64): column 0 the mean
+ * over the samples of the probability that output 0's event (the target
+ * switching) does NOT happen, sigmoid(-z_0); columns k >= 1 the mean
+ * probability of their event, sigmoid(z_k).  Each probability is formed from
+ * the logit with full relative precision on both tails and summed in FP64 in
+ * a fixed order, so a run is reproducible.  X and rates are both host, or both
+ * device if on_device (stream-ordered).  BPM_ERR_ARG for a bad handle, a NULL
+ * pointer or a count below 1. */
+int bpm_surrogate_screen(bpm_ctx* ctx, int32_t sid, const float* X, int64_t n_designs, int32_t n_jitter,
+                         double* rates, int on_device);
 /* Checkpoint of weights, Adam moments and step count; load needs the same shape. */
 int bpm_surrogate_save(bpm_ctx* ctx, int32_t sid, const char* path);
 int bpm_surrogate_load(bpm_ctx* ctx, int32_t sid, const char* path);

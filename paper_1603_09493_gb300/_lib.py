@@ -119,6 +119,7 @@ PROTOTYPES = {
     "bpm_surrogate_train": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_int64, POINTER(bpm_train_cfg),
                                     c_void_p]),
     "bpm_surrogate_infer": (c_int, [c_void_p, c_int32, c_void_p, c_int64, c_void_p, c_int]),
+    "bpm_surrogate_screen": (c_int, [c_void_p, c_int32, c_void_p, c_int64, c_int32, c_void_p, c_int]),
     "bpm_surrogate_save": (c_int, [c_void_p, c_int32, c_char_p]),
     "bpm_surrogate_load": (c_int, [c_void_p, c_int32, c_char_p]),
     "bpm_surrogate_destroy": (c_int, [c_void_p, c_int32]),

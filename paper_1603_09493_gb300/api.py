@@ -229,6 +229,24 @@ class Surrogate:
         L.check(self.lib.bpm_surrogate_infer(self.ctx.h, self.sid, L.ptr(X), X.shape[0], L.ptr(P), on_dev))
         return P
 
+    def screen(self, X, n_designs: int, n_jitter: int):
+        """Screened error rates per design [n_designs][n_out] (float64) from the
+        design-major jitter samples X [n_designs * n_jitter][n_in]: column 0 the
+        mean probability that the target island does not switch, the others the
+        mean probability of their event (bpm_surrogate_screen)."""
+        n_designs, n_jitter = int(n_designs), int(n_jitter)
+        if X.shape[0] != n_designs * n_jitter:
+            raise ValueError(f"{X.shape[0]} rows for {n_designs} designs x {n_jitter} jitter samples")
+        on_dev = int(hasattr(X, "data_ptr"))
+        if on_dev:
+            import torch
+            R = torch.empty((n_designs, self.n_out), dtype=torch.float64, device=X.device)
+        else:
+            X = np.ascontiguousarray(X, np.float32)
+            R = np.zeros((n_designs, self.n_out), np.float64)
+        L.check(self.lib.bpm_surrogate_screen(self.ctx.h, self.sid, L.ptr(X), n_designs, n_jitter, L.ptr(R), on_dev))
+        return R
+
     def save(self, path: str):
         L.check(self.lib.bpm_surrogate_save(self.ctx.h, self.sid, path.encode()))
 

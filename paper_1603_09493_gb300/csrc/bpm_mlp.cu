@@ -251,7 +251,9 @@ __nv_bfloat16** device_ptr_table(const std::vector<__nv_bfloat16*>& v, int* err)
 }
 
 // forward over `rows` (multiple of 128) batch rows, nb of them valid, input already in H[0]/HT[0]
-int forward(Mlp* m, cudaStream_t s, int rows, int nb, bool probs) {
+// infer: skip the pre-activations and transposes kept for the backward pass;
+// sigmoid: probabilities instead of logits in m->logits
+int forward(Mlp* m, cudaStream_t s, int rows, int nb, bool infer, bool sigmoid) {
     for (int l = 0; l < m->L; ++l) {
         TcEpilogue e{};
         e.bias = m->params + m->b_off[l];
@@ -259,17 +261,17 @@ int forward(Mlp* m, cudaStream_t s, int rows, int nb, bool probs) {
         e.cols_valid = m->out_real[l];
         if (l < m->L - 1) {
             // the pre-activation z and the transposed activations serve the backward pass only
-            e.C = probs ? nullptr : m->Z[l];
+            e.C = infer ? nullptr : m->Z[l];
             e.ldc = m->out_pad[l];
             e.H = m->H[l + 1];
             e.ldh = m->in_pad[l + 1];
-            e.HT = probs ? nullptr : m->HT[l + 1];
+            e.HT = infer ? nullptr : m->HT[l + 1];
             e.ldht = rows;
             BPM_TRY(gemm_tc(s, TC_EPI_BIAS_GELU, rows, m->out_pad[l], m->in_pad[l], m->H[l], m->W[l], e, m->err));
         } else {
             e.C = m->logits;
             e.ldc = m->n_out;
-            e.sigmoid = probs ? 1 : 0;
+            e.sigmoid = sigmoid ? 1 : 0;
             BPM_TRY(gemm_tc(s, TC_EPI_BIAS_OUT, rows, m->out_pad[l], m->in_pad[l], m->H[l], m->W[l], e, m->err));
         }
     }
@@ -314,6 +316,35 @@ int backward(Mlp* m, cudaStream_t s, int rows, int nb, float* loss_slot) {
         std::swap(dzT, dznT);
     }
     return BPM_OK;
+}
+
+// Screened error rates (Sec. II.C), one chunk of rows [r0, r0 + nb) of the
+// design-major sample list: one warp per (design, output) that has samples in
+// the chunk adds its share to acc[d][k] in FP64, lanes strided over the
+// samples and a fixed shuffle tree, so the sums do not depend on scheduling.
+// Output 0 counts the target island not switching, sigmoid(-z); the others
+// their own event, sigmoid(z).  Both tails keep full relative precision.
+__global__ void k_screen_accum(const float* __restrict__ z, long long r0, int nb, int J, int n_out, long long d_lo,
+                               int n_d, double* __restrict__ acc) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n_d * n_out) return;
+    const long long d = d_lo + warp / n_out;
+    const int k = warp % n_out;
+    const long long lo = max(d * J, r0), hi = min((d + 1) * J, r0 + nb);
+    double sum = 0.0;
+    for (long long r = lo + lane; r < hi; r += 32) {
+        double x = (double)z[(r - r0) * n_out + k];
+        if (k == 0) x = -x;
+        const double e = exp(-fabs(x));
+        sum += x >= 0.0 ? 1.0 / (1.0 + e) : e / (1.0 + e);
+    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) acc[d * n_out + k] += sum;
+}
+
+__global__ void k_screen_mean(double* acc, long long n, int J) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) acc[i] /= (double)J;
 }
 
 int check_err(Mlp* m, cudaStream_t s) {
@@ -479,7 +510,7 @@ int bpm_surrogate_grad(bpm_ctx* ctx, int32_t sid, const float* X, const float* Y
     BPM_CK(cudaMemcpyAsync(Yd, Y, sizeof(float) * (size_t)N * m->n_out, cudaMemcpyHostToDevice, s));
     const int rows = rup(N, 128);
     int r = load_batch(ctx, m, Xd, Yd, N, rows);
-    if (r == BPM_OK) r = forward(m, s, rows, N, false);
+    if (r == BPM_OK) r = forward(m, s, rows, N, false, false);
     if (r == BPM_OK) r = backward(m, s, rows, N, m->loss);
     cudaFreeAsync(Xd, s);
     cudaFreeAsync(Yd, s);
@@ -522,7 +553,7 @@ int bpm_surrogate_train(bpm_ctx* ctx, int32_t sid, const float* X, const float* 
             const int nb = (int)std::min<long long>(cfg->batch, N - s0);
             const int rows = rup(nb, 128);
             r = load_batch(ctx, m, Xd + s0 * m->n_in, Yd + s0 * m->n_out, nb, rows);
-            if (r == BPM_OK) r = forward(m, s, rows, nb, false);
+            if (r == BPM_OK) r = forward(m, s, rows, nb, false, false);
             if (r == BPM_OK) r = backward(m, s, rows, nb, curve + step);
             if (r != BPM_OK) break;
             m->t += 1;
@@ -575,7 +606,7 @@ int bpm_surrogate_infer(bpm_ctx* ctx, int32_t sid, const float* X, int64_t N, fl
         const int nb = (int)std::min<long long>(chunk, N - s0);
         const int rows = rup(nb, 128);
         r = load_batch(ctx, m, Xd + s0 * m->n_in, nullptr, nb, std::max(rows, std::min(rup(chunk, 128), rows)));
-        if (r == BPM_OK) r = forward(m, s, rows, nb, true);
+        if (r == BPM_OK) r = forward(m, s, rows, nb, true, true);
         if (r == BPM_OK) {
             cudaError_t e = cudaMemcpyAsync(P + s0 * m->n_out, m->logits, sizeof(float) * (size_t)nb * m->n_out,
                                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
@@ -586,6 +617,65 @@ int bpm_surrogate_infer(bpm_ctx* ctx, int32_t sid, const float* X, int64_t N, fl
         }
     }
     if (Xtmp) cudaFreeAsync(Xtmp, s);
+    if (r != BPM_OK) return r;
+    if (!on_device) return check_err(m, s);
+    return BPM_OK;
+}
+
+int bpm_surrogate_screen(bpm_ctx* ctx, int32_t sid, const float* X, int64_t n_designs, int32_t n_jitter,
+                         double* rates, int on_device) {
+    Mlp* m = get_mlp(ctx, sid);
+    if (!m || !X || !rates || n_designs < 1 || n_jitter < 1) {
+        set_error("bad surrogate screening arguments");
+        return BPM_ERR_ARG;
+    }
+    BPM_CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const long long N = (long long)n_designs * n_jitter;
+    const int chunk = 65536;
+    const float* Xd = X;
+    float* Xtmp = nullptr;
+    double* acc = nullptr;
+    const size_t out_bytes = sizeof(double) * (size_t)n_designs * m->n_out;
+    if (!on_device) {
+        BPM_CK(cudaMallocAsync(&Xtmp, sizeof(float) * (size_t)N * m->n_in, s));
+        BPM_CK(cudaMemcpyAsync(Xtmp, X, sizeof(float) * (size_t)N * m->n_in, cudaMemcpyHostToDevice, s));
+        Xd = Xtmp;
+        BPM_CK(cudaMallocAsync(&acc, out_bytes, s));
+    } else {
+        acc = rates;
+    }
+    BPM_CK(cudaMemsetAsync(acc, 0, out_bytes, s));
+    int r = BPM_OK;
+    for (long long s0 = 0; s0 < N && r == BPM_OK; s0 += chunk) {
+        const int nb = (int)std::min<long long>(chunk, N - s0);
+        const int rows = rup(nb, 128);
+        r = load_batch(ctx, m, Xd + s0 * m->n_in, nullptr, nb, std::max(rows, std::min(rup(chunk, 128), rows)));
+        if (r == BPM_OK) r = forward(m, s, rows, nb, true, false);
+        if (r == BPM_OK) {
+            const long long d_lo = s0 / n_jitter, d_hi = (s0 + nb - 1) / n_jitter;
+            const int n_d = (int)(d_hi - d_lo + 1);
+            const long long threads = 32LL * n_d * m->n_out;
+            k_screen_accum<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(m->logits, s0, nb, n_jitter, m->n_out,
+                                                                            d_lo, n_d, acc);
+            if (cudaGetLastError() != cudaSuccess) {
+                set_error("screening kernel launch failed");
+                r = BPM_ERR_CUDA;
+            }
+        }
+    }
+    if (r == BPM_OK) {
+        const long long n = (long long)n_designs * m->n_out;
+        k_screen_mean<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, n, n_jitter);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(rates, acc, out_bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
+            set_error("screening: %s", cudaGetErrorString(e));
+            r = BPM_ERR_CUDA;
+        }
+    }
+    if (Xtmp) cudaFreeAsync(Xtmp, s);
+    if (!on_device && acc) cudaFreeAsync(acc, s);
     if (r != BPM_OK) return r;
     if (!on_device) return check_err(m, s);
     return BPM_OK;

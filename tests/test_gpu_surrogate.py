@@ -116,3 +116,53 @@ def test_trained_surrogate_beats_prevalence(ctx):
     print(f"bce {bce:.3f} vs constant {bce0:.3f}, accuracy {acc:.3f}")
     assert bce < 0.5 * bce0 and acc > 0.9
     sur.destroy()
+
+
+def test_screened_rates_match_oracle(ctx):
+    # per-design means over jitter samples (Sec. II.C error rates) against the FP64 oracle at the
+    # BF16-rounded weights and inputs; the bound is that of single-sample inference, 0.02
+    params = synth.mlp_init_params(SIZES, seed=11)
+    sur = ctx.surrogate(CFG, params)
+    Pt = synth.unflatten_params(bf16_round(sur.params()), SIZES)
+    for D, J in ((37, 7), (129, 1021)):                      # ragged; 131709 rows over three 65536-row chunks
+        X, _ = dataset(D * J, 20 + J)
+        R = sur.screen(X, D, J)
+        ref = omlp.screened_ber(Pt, bf16_round(X).astype(np.float64), D, J)
+        err = np.abs(R - ref).max()
+        print(f"screen D={D} J={J}: max |d rate| {err:.2e}")
+        assert R.shape == (D, 2) and err <= 0.02
+        assert np.array_equal(sur.screen(X, D, J), R)          # fixed summation order
+    # one sample per design: the rates are 1 - p and p of inference
+    X, _ = dataset(300, 31)
+    R, P = sur.screen(X, 300, 1), sur.infer(X).astype(np.float64)
+    assert np.abs(R[:, 0] - (1.0 - P[:, 0])).max() <= 1e-6 and np.abs(R[:, 1] - P[:, 1]).max() <= 1e-6
+    # device inputs give the host result
+    import torch
+    Xd = torch.from_numpy(X).cuda()
+    assert np.array_equal(sur.screen(Xd, 300, 1).cpu().numpy(), R)
+    sur.destroy()
+
+
+def test_screened_rate_keeps_its_tail(ctx):
+    # a constant network with output biases (40, -30): every logit is exactly the bias, and the write
+    # error rate sigmoid(-40) = 4.2e-18 survives (1 - sigmoid(40) would round to 0 in any precision)
+    flat = np.zeros_like(synth.mlp_init_params(SIZES, seed=0))
+    flat[-2:] = [40.0, -30.0]
+    sur = ctx.surrogate(CFG, flat)
+    X, _ = dataset(5 * 9, 3)
+    R = sur.screen(X, 5, 9)
+    assert np.all(np.abs(R[:, 0] / (1.0 / (1.0 + np.exp(40.0))) - 1.0) <= 1e-12)
+    assert np.all(np.abs(R[:, 1] / (1.0 / (1.0 + np.exp(30.0))) - 1.0) <= 1e-12)
+    sur.destroy()
+
+
+def test_screen_rejects_bad_arguments(ctx):
+    sur = ctx.surrogate(CFG, synth.mlp_init_params(SIZES, seed=0))
+    X, _ = dataset(8, 1)
+    R = np.zeros((8, 2))
+    assert ctx.lib.bpm_surrogate_screen(ctx.h, sur.sid, L.ptr(X), 0, 8, L.ptr(R), 0) == L.BPM_ERR_ARG
+    assert ctx.lib.bpm_surrogate_screen(ctx.h, sur.sid, L.ptr(X), 8, 0, L.ptr(R), 0) == L.BPM_ERR_ARG
+    assert ctx.lib.bpm_surrogate_screen(ctx.h, sur.sid + 99, L.ptr(X), 1, 8, L.ptr(R), 0) == L.BPM_ERR_ARG
+    with pytest.raises(ValueError):
+        sur.screen(X, 3, 3)
+    sur.destroy()
