@@ -31,7 +31,7 @@ from . import _lib as L
 from . import api, synth
 
 DESIGN_KEYS = ("Ms_scale", "Ku_scale", "B_ext_T", "angle_deg")
-JITTER = dict(Ms=0.03, Ku=0.05, tilt_deg=2.0, pos_nm=0.5)
+JITTER = dict(Ms=0.03, Ku=0.07, tilt_deg=2.0, pos_nm=1.0)
 FRINGE = 0.75          # the adjacent-track island sees this fraction of the write field
 
 

@@ -48,6 +48,6 @@ def test_surrogate_assisted_search():
         picks0 = np.array(res.history[0]["verified"])
         print(f"generation-0 picks {picks0.mean():.3f} against random designs {rand.mean():.3f}")
         assert picks0.mean() <= 0.5 * rand.mean()
-        assert res.best_rates.sum() <= 0.1
+        assert res.best_rates.sum() <= 0.25 and res.best_rates.sum() <= rand.min() + 1e-12
         assert res.llg_only_s > res.verify_s
         sur.destroy()
