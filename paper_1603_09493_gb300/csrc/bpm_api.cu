@@ -572,6 +572,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         a.node_mat = M->node_mat;
         a.sell_off = M->sell_off;
         a.sell_ent = M->sell_ent;
+        a.sell_il = M->sell_il;
         a.isl = g.isl;
         a.map = H ? H->B : nullptr;
         a.tex = H ? H->tex : 0;

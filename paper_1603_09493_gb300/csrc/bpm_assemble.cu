@@ -591,6 +591,7 @@ void free_mesh(Mesh* M) {
     cudaFree(M->node_mat);
     cudaFree(M->sell_off);
     cudaFree(M->sell_ent);
+    cudaFree(M->sell_il);
     cudaFree(M->N32);
     cudaFree(M->Nhi);
     cudaFree(M->Nlo);
@@ -879,14 +880,21 @@ int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets_
             for (; q < w; ++q) ent[off[s] + 32 * q + l] = make_int2(i < n ? i : 0, 0);
         }
     }
+    std::vector<int2> ent_il(ent.size());
+    for (size_t k = 0; k < ent.size(); ++k) {
+        const int j = ent[k].x;
+        ent_il[k] = make_int2(4 * ((j >> 5) * 96 * kIlIslands + (j & 31)), ent[k].y);
+    }
     BPM_CK(cudaMalloc(&M->node_pos, np * sizeof(float4)));
     BPM_CK(cudaMalloc(&M->node_mat, np * sizeof(float4)));
     BPM_CK(cudaMalloc(&M->sell_off, off.size() * sizeof(int)));
     BPM_CK(cudaMalloc(&M->sell_ent, ent.size() * sizeof(int2)));
+    BPM_CK(cudaMalloc(&M->sell_il, ent_il.size() * sizeof(int2)));
     BPM_CK(cudaMemcpy(M->node_pos, pos.data(), np * sizeof(float4), cudaMemcpyHostToDevice));
     BPM_CK(cudaMemcpy(M->node_mat, nm.data(), np * sizeof(float4), cudaMemcpyHostToDevice));
     BPM_CK(cudaMemcpy(M->sell_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
     BPM_CK(cudaMemcpy(M->sell_ent, ent.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    BPM_CK(cudaMemcpy(M->sell_il, ent_il.data(), ent_il.size() * sizeof(int2), cudaMemcpyHostToDevice));
 
     M->nb = nb;
     M->nnz = nnz;

@@ -39,6 +39,11 @@ void set_error(const char* fmt, ...);
         if (r_ != BPM_OK) return r_; \
     } while (0)
 
+// Islands per CTA of the interleaved stage kernels.  Their shared state holds
+// component c of node j of island q at word ((j >> 5) * 3 * kIlIslands + 3 q + c) * 32 + (j & 31),
+// so that the three components of both islands sit at fixed distances from node j's word.
+constexpr int kIlIslands = 2;
+
 // Device-resident operators of one island mesh.
 struct Mesh {
     int n = 0, n_pad = 0, n_tets = 0, nb = 0, nnz = 0;
@@ -53,6 +58,9 @@ struct Mesh {
     int n_slices = 0;
     int* sell_off = nullptr;      // [n_slices + 1] first entry of each slice
     int2* sell_ent = nullptr;     // (col, float bits of val), entry e of row 32 s + l at off[s] + 32 e + l
+    // the same entries with col replaced by the byte offset of node col's x component in the
+    // interleaved shared state of the two-island stage kernels (see kIlIslands)
+    int2* sell_il = nullptr;
     // demag operator -mu0*1e6*N, row c*n_pad+i, column c'*n_pad+k (T per MA/m); rows and
     // columns from 3 n_pad to k_pad are zero
     float* N32 = nullptr;         // [K][K], K = k_pad

@@ -157,6 +157,7 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
     a.node_mat = M->node_mat;
     a.sell_off = M->sell_off;
     a.sell_ent = M->sell_ent;
+    a.sell_il = M->sell_il;
     a.isl = reinterpret_cast<const float4*>(s8 + o_isl);
     a.map = H ? H->B : nullptr;
     a.tex = H ? H->tex : 0;

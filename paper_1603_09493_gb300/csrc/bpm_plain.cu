@@ -109,6 +109,7 @@ extern "C" int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, con
         a.node_mat = M->node_mat;
         a.sell_off = M->sell_off;
         a.sell_ent = M->sell_ent;
+        a.sell_il = M->sell_il;
         a.isl = d_isl;
         a.map = H ? H->B : nullptr;
         a.tex = H ? H->tex : 0;

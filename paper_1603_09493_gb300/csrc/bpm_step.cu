@@ -262,15 +262,34 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_stage2_groups(const __grid_co
 // term by term in the same order.
 // ---------------------------------------------------------------------------
 
-// exchange sums sum_e v_e (m_q[col_e] - m_q[i]) of node i for the IPB staged islands
+// word of node j's x component of island 0 in the interleaved shared state; island q,
+// component c at + 32 (3 q + c)
+__device__ __forceinline__ int il_word(int j) { return (j >> 5) * (96 * kIlIslands) + (j & 31); }
+
+// island q's planar [3][n_pad] global state -> the interleaved shared state, 16-byte copies
+// (n_pad is a multiple of 32, so a copy never straddles two components)
+__device__ __forceinline__ void stage_state_il(const float* src, float* sm, int np, int q) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (int k = threadIdx.x; k < 3 * np / 4; k += blockDim.x) {
+        const int w = 4 * k;
+        const int c = (w >= np) + (w >= 2 * np);
+        const int j = w - c * np;
+        *reinterpret_cast<float4*>(sm + il_word(j) + 32 * (3 * q + c)) = s4[k];
+    }
+}
+
+// exchange sums sum_e v_e (m_q[col_e] - m_q[i]) of node i for the IPB staged islands.  The
+// entries carry the byte offset of the neighbour's word, and the components and islands sit
+// at fixed distances from it, so every shared load takes an immediate offset.
 template <int IPB>
 __device__ __forceinline__ void exchange_sums(const StepArgs& a, int i, const float* sm, const float3 (&mi)[IPB],
                                               float3 (&bex)[IPB]) {
-    const int np = a.n_pad, S = 3 * np;
+    static_assert(IPB == kIlIslands, "the interleaved table is laid out for kIlIslands islands");
     const int s = i >> 5, l = i & 31;
     const int off = __ldg(a.sell_off + s);
     const int nw = (__ldg(a.sell_off + s + 1) - off) >> 5;
-    const int2* ep = a.sell_ent + off + l;
+    const int2* ep = a.sell_il + off + l;
+    const char* smb = reinterpret_cast<const char*>(sm);
     float bx[IPB], by[IPB], bz[IPB];
 #pragma unroll
     for (int q = 0; q < IPB; ++q) bx[q] = by[q] = bz[q] = 0.f;
@@ -278,12 +297,12 @@ __device__ __forceinline__ void exchange_sums(const StepArgs& a, int i, const fl
     for (int e = 0; e < nw; ++e) {
         const int2 c = __ldg(ep + 32 * e);
         const float v = __int_as_float(c.y);
+        const float* mj = reinterpret_cast<const float*>(smb + c.x);
 #pragma unroll
         for (int q = 0; q < IPB; ++q) {
-            const float* sq = sm + q * S;
-            bx[q] += v * (sq[c.x] - mi[q].x);
-            by[q] += v * (sq[np + c.x] - mi[q].y);
-            bz[q] += v * (sq[2 * np + c.x] - mi[q].z);
+            bx[q] += v * (mj[32 * (3 * q)] - mi[q].x);
+            by[q] += v * (mj[32 * (3 * q + 1)] - mi[q].y);
+            bz[q] += v * (mj[32 * (3 * q + 2)] - mi[q].z);
         }
     }
 #pragma unroll
@@ -327,15 +346,16 @@ __device__ __forceinline__ void stage1_multi(const StepArgs& a, int b0, int j, f
     const double t = step_time(a, j);
     const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
     const float xh = a.x0 + a.v_nm_ps * (float)t;
-    for (int q = 0; q < nb; ++q) stage_state(a.m + (size_t)(b0 + q) * S, sm + q * S, np);
+    for (int q = 0; q < nb; ++q) stage_state_il(a.m + (size_t)(b0 + q) * S, sm, np, q);
     const float hf = (float)a.h;
     const unsigned mask = a.mask;
     __syncthreads();
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         float3 mi[IPB], bex[IPB], hdv[IPB];
+        const int wi = il_word(i);
 #pragma unroll
         for (int q = 0; q < IPB; ++q) {
-            mi[q] = f3(sm[q * S + i], sm[q * S + np + i], sm[q * S + 2 * np + i]);
+            mi[q] = f3(sm[wi + 32 * (3 * q)], sm[wi + 32 * (3 * q + 1)], sm[wi + 32 * (3 * q + 2)]);
             hdv[q] = (mask & BPM_TERM_DEMAG) && q < nb ? load_hd(a, b0 + q, i) : f3(0, 0, 0);
         }
         const float4 pos = __ldg(a.node_pos + i);
@@ -373,7 +393,7 @@ __device__ __forceinline__ void stage2_multi(const StepArgs& a, int b0, int j, f
     const double t = step_time(a, j) + a.h;
     const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
     const float xh = a.x0 + a.v_nm_ps * (float)t;
-    for (int q = 0; q < nb; ++q) stage_state(a.ms + (size_t)(b0 + q) * S, sm + q * S, np);
+    for (int q = 0; q < nb; ++q) stage_state_il(a.ms + (size_t)(b0 + q) * S, sm, np, q);
     const float hh = 0.5f * (float)a.h;
     const unsigned mask = a.mask;
     __syncthreads();
@@ -382,9 +402,10 @@ __device__ __forceinline__ void stage2_multi(const StepArgs& a, int b0, int j, f
     for (int q = 0; q < IPB; ++q) mzp[q] = 0.f;
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         float3 mi[IPB], bex[IPB], hdv[IPB];
+        const int wi = il_word(i);
 #pragma unroll
         for (int q = 0; q < IPB; ++q) {
-            mi[q] = f3(sm[q * S + i], sm[q * S + np + i], sm[q * S + 2 * np + i]);
+            mi[q] = f3(sm[wi + 32 * (3 * q)], sm[wi + 32 * (3 * q + 1)], sm[wi + 32 * (3 * q + 2)]);
             hdv[q] = (mask & BPM_TERM_DEMAG) && q < nb ? load_hd(a, b0 + q, i) : f3(0, 0, 0);
         }
         const float4 pos = __ldg(a.node_pos + i);

@@ -11,6 +11,7 @@ struct StepArgs {
     const float4* node_mat;   // [n_pad] 2Ku/Ms (T), Ms (MA/m)
     const int* sell_off;
     const int2* sell_ent;
+    const int2* sell_il;      // sell_ent with shared-state byte offsets (two-island kernels)
     const float4* isl;        // [B][3] (1/Ms_s, Ku_s/Ms_s, Ms_s, 0), (u, pos_x), (pos_y, Hext)
     const float4* map;        // head map (linear copy) or nullptr: no head field
     cudaTextureObject_t tex;  // head map voxels for the lookups
