@@ -52,10 +52,11 @@ def config_dict(mesh, k, precision, B, n_gpus):
             "l2": "per-step working set (state, stages, demag operand and field, BF16/FP32 operator) > 129 MB L2"}
 
 
-def sample_clocks_start():
+def sample_clocks_start(log_path: str = ""):
+    """nvidia-smi clock samples every 100 ms until sample_clocks_stop; the raw
+    samples also go to log_path when one is given."""
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
+        f = open(log_path or os.devnull, "w")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -401,7 +402,7 @@ def main_uneven(args):
     for _ in range(max(args.warmup, 1)):
         bt.advance(1)
     torch.cuda.synchronize()
-    proc, cf = sample_clocks_start()
+    proc, cf = sample_clocks_start(args.clock_log)
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -524,7 +525,7 @@ def main(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    proc, cf = sample_clocks_start()
+    proc, cf = sample_clocks_start(args.clock_log)
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -632,4 +633,5 @@ if __name__ == "__main__":
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", default="census", choices=["census", "uneven", "extras", "surrogate"])
     ap.add_argument("--realisations", type=int, default=512)
+    ap.add_argument("--clock-log", default="", help="also write the raw nvidia-smi clock samples here")
     sys.exit(main(ap.parse_args()))
