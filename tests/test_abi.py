@@ -53,6 +53,43 @@ def test_struct_layouts_match_the_header(tmp_path):
     assert L.ISLAND_DTYPE.itemsize == ctypes.sizeof(L.bpm_island) == 44
 
 
+def test_every_struct_matches_its_ctypes_twin(tmp_path):
+    # every field offset and every size, for each header struct the binding mirrors
+    structs = [getattr(L, n) for n in dir(L) if n.startswith("bpm_") and isinstance(getattr(L, n), type)
+               and issubclass(getattr(L, n), ctypes.Structure)]
+    assert len(structs) >= 8
+    lines, want = [], []
+    for st in structs:
+        lines.append(f'printf("%zu\\n", sizeof({st.__name__}));')
+        want.append(ctypes.sizeof(st))
+        for fname, _ in st._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({st.__name__}, {fname}));')
+            want.append(getattr(st, fname).offset)
+    src = tmp_path / "layout.c"
+    src.write_text('#include "bpm.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){\n' +
+                   "\n".join(lines) + "\nreturn 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-pedantic", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == want
+
+
+def test_a_c_program_links_every_declared_function(lib, tmp_path):
+    # the declarations, compiled as C99, resolve against the built library
+    names = _declared()
+    src = tmp_path / "link.c"
+    src.write_text('#include "bpm.h"\n#include <stdio.h>\nint main(void){\n' +
+                   "\n".join(f'printf("%p\\n", (void*){n});' for n in names) + "\nreturn 0;}\n")
+    exe = tmp_path / "link"
+    libdir = os.path.dirname(L.LIB_PATH)
+    subprocess.check_call(["gcc", "-std=c99", "-pedantic", "-Wall", "-Werror", "-Wno-pedantic",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lbpmllg",
+                           f"-Wl,-rpath,{libdir}"])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and len(out.stdout.split()) == len(names)
+
+
 def test_no_gpu_calls_fail_cleanly(lib):
     # without a GPU the library reports an error instead of crashing
     import torch
