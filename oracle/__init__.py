@@ -14,7 +14,7 @@ Modules
   demag     Fredkin-Koehler FEM/BEM demagnetising operator (Lindholm weights)
   headfield trilinear lookup of the write-head field map
   llg       effective field, Heun integrator with renormalisation, switch detector
-  mlp       surrogate MLP forward/backward, BCE loss, AdamW
+  mlp       surrogate MLP forward/backward, BCE loss, AdamW, screened error rates
   ber       bit-error-rate formulas of Sec. II.C (Eqs. 1-3)
   hcrit     critical-field search of Sec. II.C
   neb       nudged elastic band for the adjacent-track barrier (Sec. II.C, Eq. 3)
