@@ -275,6 +275,15 @@ int bpm_batch_destroy(bpm_batch* bt);
 int bpm_run_batch(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p,
                   int32_t n_intervals, float* m_final, int32_t ld, uint8_t* switched,
                   float* t_sw_ps, int32_t* status);
+/* The same run with the outputs in caller-owned DEVICE buffers of the context's
+ * device (layouts as in bpm_batch_read; any output may be NULL); the island
+ * table isl stays a host array.  The copies are ordered on the context stream,
+ * and the call returns after that stream has drained (the batch's scratch is
+ * freed), so the outputs are ready when it returns.  Errors as bpm_run_batch,
+ * including BPM_ERR_TIMEOUT for a timed-out GEMM wait. */
+int bpm_run_batch_dev(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p,
+                      int32_t n_intervals, float* m_final, int32_t ld, uint8_t* switched,
+                      float* t_sw_ps, int32_t* status);
 
 /* The plain form: every island integrated on its own, one island per launch,
  * with an FP32 matrix-vector demag product streaming the operator from HBM in

@@ -110,6 +110,8 @@ PROTOTYPES = {
     "bpm_batch_destroy": (c_int, [c_void_p]),
     "bpm_run_batch": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,
                               c_void_p, c_void_p, c_void_p]),
+    "bpm_run_batch_dev": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,
+                                  c_void_p, c_void_p, c_void_p]),
     "bpm_run_plain": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,
                               c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
     "bpm_surrogate_create": (c_int, [c_void_p, POINTER(bpm_mlp_cfg), c_void_p, POINTER(c_int32)]),

@@ -53,6 +53,7 @@ class Context:
         s = None if stream is None else c_void_p(int(getattr(stream, "cuda_stream", stream)))
         L.check(self.lib.bpm_create(byref(h), int(device), s))
         self.h = h
+        self.device = int(device)
 
     def close(self):
         if self.h:
@@ -123,6 +124,22 @@ class Context:
         L.check(self.lib.bpm_run_batch(self.h, L.ptr(isl), B, byref(q), int(n_intervals), L.ptr(m), n,
                                        L.ptr(sw), L.ptr(tsw), L.ptr(st)))
         return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st)
+
+    def run_batch_dev(self, islands, params, n_intervals, precision=L.PREC_BF16X3, map_id=-1):
+        """bpm_run_batch with the results in torch device tensors on the context's device."""
+        import torch
+        isl = island_array(islands)
+        q = run_params(params, precision, map_id)
+        n = max(self.mesh_info(int(mid))["n_nodes"] for mid in np.unique(isl["mesh_id"]))
+        B = len(isl)
+        dev = torch.device("cuda", self.device)
+        m = torch.empty((B, 3, n), dtype=torch.float32, device=dev)
+        sw = torch.empty(B, dtype=torch.uint8, device=dev)
+        tsw = torch.empty(B, dtype=torch.float32, device=dev)
+        st = torch.empty(B, dtype=torch.int32, device=dev)
+        L.check(self.lib.bpm_run_batch_dev(self.h, L.ptr(isl), B, byref(q), int(n_intervals), L.ptr(m), n,
+                                           L.ptr(sw), L.ptr(tsw), L.ptr(st)))
+        return dict(m=m, switched=sw.bool(), t_sw=tsw, status=st)
 
     def run_plain(self, islands, params, n_intervals, map_id=-1):
         """One island per launch, FP32 GEMV demag (bpm_run_plain); returns results and device ms."""

@@ -1080,4 +1080,24 @@ int bpm_run_batch(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_
     return r;
 }
 
+int bpm_run_batch_dev(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p, int32_t n_intervals,
+                      float* m_final, int32_t ld, uint8_t* switched, float* t_sw_ps, int32_t* status) {
+    bpm_batch* bt = nullptr;
+    BPM_TRY(bpm_batch_create(ctx, isl, B, p, &bt));
+    int r = bpm_batch_advance(bt, n_intervals);
+    if (r == BPM_OK) r = bpm_batch_read(bt, m_final, ld, switched, t_sw_ps, status, nullptr, 1);
+    int gerr = 0;
+    if (r == BPM_OK && cudaMemcpyAsync(&gerr, bt->gemm_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) !=
+                           cudaSuccess) {
+        set_error("reading the GEMM error flag failed");
+        r = BPM_ERR_CUDA;
+    }
+    bpm_batch_destroy(bt);   // synchronises the stream before it frees the batch
+    if (r == BPM_OK && gerr) {
+        set_error("a bounded wait in the tensor-core GEMM gave up (code %d)", gerr);
+        r = BPM_ERR_TIMEOUT;
+    }
+    return r;
+}
+
 }  // extern "C"

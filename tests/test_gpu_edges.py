@@ -182,3 +182,20 @@ def test_stoner_wohlfarth_switching_field_at_45_degrees(ctx):
     out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_FP32)
     print("switched", out["switched"], "t_sw", out["t_sw"])
     assert not out["switched"][0] and out["switched"][1]
+
+
+def test_device_output_run_matches_the_host_run(ctx):
+    # bpm_run_batch_dev writes the same results into device buffers
+    mid = ctx.mesh_upload(synth.small_island_mesh(), synth.ecc_materials())
+    hid = ctx.headmap_upload(synth.synthetic_head_map())
+    isl = synth.jittered_islands(37, seed=8, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, t_end_ps=20.0, alpha=0.1, rise_ps=10.0, use_map=True, x0_nm=-2.0,
+                        uniform_T=synth.uniform_field(0.6, 165.0))
+    p.substeps = api.stable_substeps(api.field_bound(ctx, mid, isl, p, synth.synthetic_head_map()), p.dt_ps, p.alpha)
+    host = ctx.run_batch(isl, p, p.n_intervals, map_id=hid)
+    dev = ctx.run_batch_dev(isl, p, p.n_intervals, map_id=hid)
+    assert dev["m"].is_cuda and dev["switched"].is_cuda
+    assert np.array_equal(dev["m"].cpu().numpy(), host["m"])
+    assert np.array_equal(dev["switched"].cpu().numpy(), host["switched"])
+    assert np.array_equal(dev["t_sw"].cpu().numpy(), host["t_sw"])
+    assert np.array_equal(dev["status"].cpu().numpy(), host["status"])
