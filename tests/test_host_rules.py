@@ -1,6 +1,7 @@
 """Host-side rules of the binding (no GPU): the integrator step count is the
 smallest k with gamma/(1 + alpha^2) B dt / k <= 1/2 (the explicit-step bound
-Heun's method needs on the precession frequency)."""
+Heun's method needs on the precession frequency); the critical-field search of
+Sec. II.C makes the oracle search's decisions when both see the same outcomes."""
 import math
 
 import numpy as np
@@ -20,3 +21,47 @@ def test_stable_substeps_is_the_smallest_admissible_count():
     assert api.stable_substeps(800.0, 0.1, 0.1) == 28
     assert api.stable_substeps(0.0, 0.1, 0.1) == 1
     assert api.stable_substeps(1.0, 0.1, 0.0, courant=0.25) == math.ceil(gamma * 0.1 / 0.25)
+
+
+def _threshold_rule(isl, role):
+    # closed-form stand-in for the LLG switched flags: the bad outcome starts once |H_ext| reaches
+    # the island's threshold (carried in Ku_scale, in tesla); bad is "not switched" for the target
+    # bit and "switched" for the previous bit
+    h = np.linalg.norm(isl.Hext_T.astype(np.float64), axis=1)
+    bad = h >= isl.Ku_scale.astype(np.float64)
+    return ~bad if role == "targ" else bad                  # targ: good = switched; prev: good = not
+
+
+def test_critical_field_search_matches_the_oracle_search(monkeypatch):
+    from oracle import hcrit as ohcrit
+    from paper_1603_09493_gb300 import hcrit, synth
+
+    sigma = np.array([0.04] * 10)
+    # thresholds in units of sigma: inside the grid, on grid points, at 0 (abort), beyond 4 sigma
+    tau = sigma * np.array([0.0, 0.3, 0.5, 1.0, 1.37, 2.25, 3.9, 4.0, 4.2, 7.0])
+    rng = np.random.default_rng(1)
+    direction = rng.standard_normal((10, 3))
+    direction /= np.linalg.norm(direction, axis=1, keepdims=True)
+    isl = synth.nominal_islands(10)
+    isl.Ku_scale = tau.astype(np.float32)
+    for role in ("targ", "prev"):
+        class FakeBatch:
+            def __init__(self, ops, sub, params, head_map=None):
+                self.sub = sub
+
+            def run(self):
+                return {"switched": _threshold_rule(self.sub, role)}
+
+        monkeypatch.setattr(ohcrit, "Batch", FakeBatch)
+        h_o, ber_o, ab_o = ohcrit.search(None, isl, None, direction, sigma, role)
+        res = hcrit.critical_field_search(lambda sub: _threshold_rule(sub, role), isl, direction, sigma, role)
+        assert np.array_equal(res.aborted, ab_o) and np.array_equal(res.h_crit_T, h_o)
+        # the same Gaussian tail, erfc on one side and 1 - erf on the other: equal up to the
+        # cancellation of 1 - erf at 4 sigma (~3e-12 relative)
+        assert np.allclose(res.ber, ber_o, rtol=1e-9, atol=0)
+        assert res.aborted.tolist() == [True] + [False] * 9 and np.all(res.ber[0] == 1.0)
+        # the last good field brackets the threshold to sigma/8 (two halvings of sigma/2); none past 4 sigma
+        inside = (tau > 0) & (tau <= 4.0 * sigma)
+        assert np.all(res.h_crit_T[inside] < tau[inside] + 1e-12)
+        assert np.all(res.h_crit_T[inside] >= tau[inside] - sigma[inside] / 8 - 1e-12)
+        assert np.all(res.h_crit_T[tau > 4.0 * sigma] == 4.0 * sigma[tau > 4.0 * sigma])
