@@ -65,3 +65,25 @@ def test_critical_field_search_matches_the_oracle_search(monkeypatch):
         assert np.all(res.h_crit_T[inside] < tau[inside] + 1e-12)
         assert np.all(res.h_crit_T[inside] >= tau[inside] - sigma[inside] / 8 - 1e-12)
         assert np.all(res.h_crit_T[tau > 4.0 * sigma] == 4.0 * sigma[tau > 4.0 * sigma])
+
+
+def test_error_rate_formulas_match_the_oracle():
+    # Eqs. 1-3 as the product computes them against the oracle's own statements of them
+    import math
+
+    from oracle import ber as ober
+    from oracle import neb as oneb
+    from paper_1603_09493_gb300 import adjacent, hcrit
+
+    for K1, Js in ((0.9e6, 1.0), (1.5e6, 0.8), (3.0e5, 1.2)):
+        assert math.isclose(hcrit.sfd_sigma_T(K1, Js), ober.sfd_sigma_T(K1, Js), rel_tol=1e-15)
+    for mult in np.linspace(0.0, 6.0, 25):
+        s = 0.035
+        assert math.isclose(hcrit.ber_from_hcrit(mult * s, s), ober.ber_from_hcrit(mult * s, s), rel_tol=1e-9)
+    E_J = np.linspace(10.0, 80.0, 15) * 1.380649e-23 * 300.0      # 10 .. 80 kT at 300 K
+    got = adjacent.ber_adj(E_J)
+    ref = np.array([ober.ber_adj(float(x)) for x in oneb.barrier_kT(E_J)])
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+    for b, e in zip(got, oneb.barrier_kT(E_J)):
+        assert math.isclose(adjacent.barrier_kT_from_ber(float(b)), float(e), rel_tol=1e-12)
+    assert adjacent.ber_tot(1e-4, 2e-5, 3e-6) == ober.ber_tot(1e-4, 2e-5, 3e-6)
