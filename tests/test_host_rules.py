@@ -89,3 +89,37 @@ def test_error_rate_formulas_match_the_oracle():
     for b, e in zip(got, oneb.barrier_kT(E_J)):
         assert math.isclose(adjacent.barrier_kT_from_ber(float(b)), float(e), rel_tol=1e-12)
     assert adjacent.ber_tot(1e-4, 2e-5, 3e-6) == ober.ber_tot(1e-4, 2e-5, 3e-6)
+
+
+def test_ego_loop_makes_the_oracle_loops_choices(monkeypatch):
+    # the product's EGO loop (theta search, search set, EI argmax, bookkeeping) with its likelihood
+    # and kriging calls answered by the oracle: it must propose exactly the oracle loop's designs
+    from oracle import ego as oego
+    from paper_1603_09493_gb300 import ego, synth
+
+    class OracleKriging:
+        def __init__(self, ctx, X, y, theta, nugget=1e-10):
+            self.gp = oego.fit(np.asarray(X, float), np.asarray(y, float), np.asarray(theta, float), nugget)
+
+        def predict(self, C, f_min):
+            return oego.predict(self.gp, np.asarray(C, float), f_min)
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            pass
+
+    monkeypatch.setattr(ego, "nll", lambda ctx, X, y, th, nugget=1e-10:
+                        np.array([oego.nll(np.asarray(X, float), np.asarray(y, float), t, nugget)
+                                  for t in np.asarray(th, float)]))
+    monkeypatch.setattr(ego, "Kriging", OracleKriging)
+    C = synth.lhs_candidates(20, 12, 2, seed=3)
+    X0 = C[oego.maximin_select(C)[0]]
+    draws = lambda it: [synth.theta_unit_draws(16, 2, 5 + it, r) for r in range(3)]
+    cands = lambda it: (synth.unit_points(300, 2, 6, 2 * it), synth.unit_points(300, 2, 6, 2 * it + 1))
+    X, y, hist = ego.ego(None, synth.branin01, X0, synth.branin01(X0), 5, draws, cands)
+    Xo, yo, histo = oego.ego(synth.branin01, X0, synth.branin01(X0), 5, draws, cands)
+    assert np.array_equal(X, Xo) and np.array_equal(y, yo)
+    for (t, e), (to, eo) in zip(hist, histo):
+        assert np.array_equal(t, to) and e == eo
