@@ -123,3 +123,13 @@ def test_ego_loop_makes_the_oracle_loops_choices(monkeypatch):
     assert np.array_equal(X, Xo) and np.array_equal(y, yo)
     for (t, e), (to, eo) in zip(hist, histo):
         assert np.array_equal(t, to) and e == eo
+
+
+def test_a_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library the binding raises before any work
+    import pytest
+
+    from paper_1603_09493_gb300 import _lib as L
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        L.load(str(tmp_path / "libbpmllg.so"))
