@@ -168,9 +168,9 @@ def cpu_baseline(mesh, mats, hm, p, k, target_s=15.0):
                       f"numpy FP64, {t:.1f} s"}
 
 
-def stable_k(ctx, mid, hm, isl, p):
-    from paper_1603_09493_gb300 import api
-    return api.stable_substeps(api.field_bound(ctx, mid, isl, p, hm), p.dt_ps, p.alpha)
+def stable_k(ctx, hid, isl, p):
+    """The library's integrator step count for this workload (bpm_stable_substeps)."""
+    return ctx.stable_substeps(isl, p, hid)[0]
 
 
 def measure_plain(ctx, isl, p, hid, prec, n, islands=8, intervals=2):
@@ -194,11 +194,11 @@ def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400, mesh=None, mats=None):
     isl = synth.jittered_islands(D, seed=4, mesh_id=mid)
     isl.pos_nm[:, 1] += 12.7
     p = synth.RunParams(dt_ps=0.1, rise_ps=0.0, v_m_per_s=0.0, x0_nm=2.0, use_map=True)
-    step = adjacent.stable_step(ctx, mid, isl, p, hm)
+    step = adjacent.stable_step(ctx, mid, isl, p, hid)
     ctx.neb(isl, P, 2, step, 1.0, -1, map_id=hid, head_x_nm=p.x0_nm)           # warm-up
     t = time.perf_counter()
     out = adjacent.barriers(ctx, isl, p, n_images=P, max_iters=iters, climb_after=iters // 2, step=step,
-                            map_id=hid, head_map=hm)
+                            map_id=hid)
     wall = time.perf_counter() - t
     kt = out["E_B_kT"]
     oracle = None
@@ -396,8 +396,7 @@ def main_uneven(args):
     hid = ctx.headmap_upload(hm)
     isl, role = synth.uneven_batch(variants, mids, realisations=args.realisations, seed=2, layout="staggered")
     p = synth.RunParams(dt_ps=DT_PS, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=-10.0, use_map=True)
-    bound = max(api.field_bound(ctx, mid, isl.subset(np.where(isl.mesh_id == mid)[0]), p, hm) for mid in mids)
-    p.substeps = api.stable_substeps(bound, p.dt_ps, p.alpha)
+    p.substeps = stable_k(ctx, hid, isl, p)
     bt = ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid)
     for _ in range(max(args.warmup, 1)):
         bt.advance(1)
@@ -511,7 +510,7 @@ def main(args):
     mid = ctx.mesh_upload(mesh, mats)
     isl.mesh_id[:] = mid
     hid = ctx.headmap_upload(hm)
-    k = stable_k(ctx, mid, hm, isl, p)
+    k = stable_k(ctx, hid, isl, p)
     p.substeps = k
     bt = ctx.batch(isl, p, precision=prec, map_id=hid)
     tuning = None

@@ -97,7 +97,8 @@ typedef struct {
 /* Run parameters shared by all islands of a batch. */
 typedef struct {
     double   dt_ps;       /* output interval (0.1 ps in the workloads) */
-    int32_t  substeps;    /* Heun steps per output interval, >= 1 (step h = dt/substeps) */
+    int32_t  substeps;    /* Heun steps per output interval (step h = dt/substeps), >= 1; or 0:
+                             the library takes the stable count of bpm_stable_substeps */
     int32_t  precision;   /* BPM_PREC_* */
     double   t0_ps;       /* start time */
     double   alpha;       /* Gilbert damping */
@@ -133,6 +134,11 @@ typedef struct {
  * BPM_ERR_CUDA if the device is absent or not sm_103. */
 int  bpm_create(bpm_ctx** out, int device, void* cuda_stream);
 void bpm_destroy(bpm_ctx* ctx);
+/* The cudaStream_t (as void*) on which the context orders its work: the one
+ * passed to bpm_create, or the library's own.  A caller that hands device
+ * buffers produced or consumed on another stream orders that stream against
+ * this one (events, cudaStreamWaitEvent) before and after the call. */
+int  bpm_context_stream(bpm_ctx* ctx, void** cuda_stream);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* bpm_last_error(void);
 /* Library version string. */
@@ -173,6 +179,29 @@ int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, i
 /* Batched LLG (Sec. II.C recording simulations, one batch of islands)     */
 /* ---------------------------------------------------------------------- */
 
+/* Integrator step count (Sec. II.A names the LLG solver but not its time step;
+ * the explicit Heun step is stable on the fastest precession mode when
+ * gamma/(1+alpha^2) |B| h <= 1/2).  For field_bound_T the largest |B_eff|
+ * (tesla) a run can see, *substeps = the smallest k >= 1 with
+ *   gamma/(1+alpha^2) * field_bound_T * dt_ps / k <= 1/2,
+ * gamma = 0.176085963023 rad/(ps T).  Host arithmetic only (no GPU needed).
+ * BPM_ERR_ARG for a negative bound, dt <= 0, alpha < 0 or a NULL output. */
+int bpm_substeps_for_bound(double field_bound_T, double dt_ps, double alpha, int32_t* substeps);
+/* The step count and field bound of a run of the islands isl [B] (host) under
+ * p (p->substeps is ignored).  The bound is the largest over the meshes of
+ * the batch of
+ *   lambda_max(S) / min Ms_scale          exchange (largest eigenvalue of the
+ *                                         mesh's exchange operator, power iteration)
+ * + max_i (2 Ku_i / Ms_i) * max (Ku_scale / Ms_scale)      anisotropy
+ * + mu0 max_i Ms_i * max Ms_scale                          demag
+ * + max |B| over the head map's voxels (when p->map_id >= 0)
+ * + |p->uniform_T| + max |Hext_T|                          applied fields
+ * with the jitter extremes taken over the islands of that mesh.  A run with
+ * p->substeps = 0 uses this k.  *field_bound_T is nullable.
+ * BPM_ERR_ARG for an unknown mesh or map id or bad jitter. */
+int bpm_stable_substeps(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p,
+                        int32_t* substeps, double* field_bound_T);
+
 /* Create a batch of B islands.  Islands may use different meshes (design
  * variants of uneven size): they are grouped by mesh, each group with its own
  * demag GEMM, and the groups of one output interval are captured into a
@@ -184,7 +213,7 @@ int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, i
  * calls use a leading dimension ld >= the largest mesh's n_nodes; entries past
  * an island's own n_nodes are not read and are left untouched (reads of host
  * arrays leave them zero).
- * Errors: BPM_ERR_ARG (B < 1, unknown mesh or map id, substeps < 1). */
+ * Errors: BPM_ERR_ARG (B < 1, unknown mesh or map id, substeps < 0). */
 int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B,
                      const bpm_run_params* p, bpm_batch** out);
 /* Set the state: m (layout above, leading dimension ld) or NULL for +z, the
@@ -296,6 +325,22 @@ int bpm_run_batch_dev(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_
 int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p,
                   int32_t n_intervals, float* m_final, int32_t ld, uint8_t* switched, float* t_sw_ps,
                   int32_t* status, double* device_ms);
+/* The plain form in FP64: one island per launch, every step of the recording
+ * simulation (Sec. II.A, II.C) in FP64 -- the effective field from the FP64
+ * exchange operator (difference form of the assembly's values), anisotropy,
+ * an FP64 matrix-vector demag product with the assembly's FP64 Fredkin-Koehler
+ * matrix, a trilinear head-map lookup in FP64 and the ramped uniform and
+ * per-island fields; Heun predictor and corrector with |m| renormalised after
+ * each; the volume-averaged m_z switch detector summed in FP64.  It is the
+ * GPU twin of an FP64 reference, one island at a time, and the FP64 baseline
+ * the batched path is measured against.  Every mesh used must have been
+ * uploaded with BPM_MESH_KEEP_F64 (BPM_ERR_STATE otherwise); p->precision is
+ * ignored.
+ *   m_final  host double [B][3][ld] (nullable)   t_sw_ps host double [B], -1 if none
+ *   switched, status, device_ms as in bpm_run_plain. */
+int bpm_run_plain_f64(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p,
+                      int32_t n_intervals, double* m_final, int32_t ld, uint8_t* switched, double* t_sw_ps,
+                      int32_t* status, double* device_ms);
 
 /* ---------------------------------------------------------------------- */
 /* Surrogate MLP (stands in for the Gaussian-process predictor of the      */

@@ -78,6 +78,10 @@ class bpm_tuning(ctypes.Structure):
 PROTOTYPES = {
     "bpm_create": (c_int, [POINTER(c_void_p), c_int, c_void_p]),
     "bpm_destroy": (None, [c_void_p]),
+    "bpm_context_stream": (c_int, [c_void_p, POINTER(c_void_p)]),
+    "bpm_substeps_for_bound": (c_int, [c_double, c_double, c_double, POINTER(c_int32)]),
+    "bpm_stable_substeps": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), POINTER(c_int32),
+                                    POINTER(c_double)]),
     "bpm_last_error": (c_char_p, []),
     "bpm_version": (c_char_p, []),
     "bpm_mesh_upload": (c_int, [c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
@@ -114,6 +118,8 @@ PROTOTYPES = {
                                   c_void_p, c_void_p, c_void_p]),
     "bpm_run_plain": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,
                               c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
+    "bpm_run_plain_f64": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), c_int32, c_void_p, c_int32,
+                                  c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
     "bpm_surrogate_create": (c_int, [c_void_p, POINTER(bpm_mlp_cfg), c_void_p, POINTER(c_int32)]),
     "bpm_surrogate_param_count": (c_int, [c_void_p, c_int32, POINTER(c_int64)]),
     "bpm_surrogate_get_params": (c_int, [c_void_p, c_int32, c_void_p]),

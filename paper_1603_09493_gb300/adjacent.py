@@ -34,24 +34,25 @@ def ber_tot(targ, prev, adj):
     return np.asarray(targ) + np.asarray(prev) + np.asarray(adj)
 
 
-def stable_step(ctx, mesh_id: int, islands, params, head_map=None, courant: float = 0.4) -> float:
+def stable_step(ctx, mesh_id: int, islands, params, map_id: int = -1, courant: float = 0.4) -> float:
     """Band step (m^3/MJ) with step * max(Ms_i) * |B|_max <= courant, the bound of the
-    explicit update on the stiffest (exchange) mode."""
-    bound = api.field_bound(ctx, mesh_id, islands, params, head_map)
+    explicit update on the stiffest (exchange) mode; |B|_max is the library's field
+    bound of the islands (bpm_stable_substeps)."""
+    bound = ctx.stable_substeps(islands, params, map_id)[1]
     Ms = ctx.get_operator(mesh_id, L.OP_NODAL_MS_F64)
     ms_max = float(np.max(Ms)) * 1e-6 * float(np.max(np.asarray(islands.Ms_scale, np.float64)))
     return courant / (ms_max * bound)
 
 
 def barriers(ctx, islands, params, n_images: int = 12, max_iters: int = 2000, climb_after: int = 400,
-             spring: float = 1.0, step=None, precision: int = L.PREC_BF16X3, map_id: int = -1, head_map=None,
+             spring: float = 1.0, step=None, precision: int = L.PREC_BF16X3, map_id: int = -1,
              force_tol: float = 0.0, T_K: float = 300.0) -> dict:
     """Energy barriers (J and kT) and BER_adj of every island in the fringing field
     of the head frozen at params.x0_nm (params.uniform_T and each island's
     Hext_T add a uniform field; params.term_mask selects the terms)."""
     mid = int(np.asarray(islands.mesh_id)[0])
     if step is None:
-        step = stable_step(ctx, mid, islands, params, head_map)
+        step = stable_step(ctx, mid, islands, params, map_id)
     out = ctx.neb(islands, n_images, max_iters, step, spring, climb_after, precision=precision, map_id=map_id,
                   head_x_nm=params.x0_nm, uniform_T=params.uniform_T, term_mask=params.term_mask,
                   force_tol=force_tol)

@@ -6,8 +6,8 @@ tensors (or anything with data_ptr()).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
-import math
 from ctypes import byref, c_double, c_int32, c_void_p
 
 import numpy as np
@@ -54,6 +54,39 @@ class Context:
         L.check(self.lib.bpm_create(byref(h), int(device), s))
         self.h = h
         self.device = int(device)
+        sp = c_void_p()
+        L.check(self.lib.bpm_context_stream(h, byref(sp)))
+        self.stream_ptr = int(sp.value or 0)
+
+    @contextlib.contextmanager
+    def device_order(self):
+        """Order a library call that reads or writes torch device tensors against
+        torch's current stream: the context stream waits for the work already
+        queued on torch's stream (the producers of the inputs, and earlier users
+        of memory the caching allocator hands out again), and torch's stream
+        waits for the call's work before anything queued after it (readers of
+        the outputs, frees of the inputs)."""
+        import torch
+        cur = torch.cuda.current_stream(self.device)
+        if int(cur.cuda_stream) == self.stream_ptr:
+            yield
+            return
+        ctx_stream = torch.cuda.ExternalStream(self.stream_ptr, device=torch.device("cuda", self.device))
+        ctx_stream.wait_stream(cur)
+        try:
+            yield
+        finally:
+            cur.wait_stream(ctx_stream)
+
+    def stable_substeps(self, islands, params, map_id: int = -1):
+        """(k, field bound in T) of a run of these islands (bpm_stable_substeps): the
+        library's integrator step count, the one a run with substeps = 0 takes."""
+        isl = island_array(islands)
+        q = run_params(params, L.PREC_FP32, map_id)
+        k = c_int32()
+        b = c_double()
+        L.check(self.lib.bpm_stable_substeps(self.h, L.ptr(isl), len(isl), byref(q), byref(k), byref(b)))
+        return k.value, b.value
 
     def close(self):
         if self.h:
@@ -137,8 +170,9 @@ class Context:
         sw = torch.empty(B, dtype=torch.uint8, device=dev)
         tsw = torch.empty(B, dtype=torch.float32, device=dev)
         st = torch.empty(B, dtype=torch.int32, device=dev)
-        L.check(self.lib.bpm_run_batch_dev(self.h, L.ptr(isl), B, byref(q), int(n_intervals), L.ptr(m), n,
-                                           L.ptr(sw), L.ptr(tsw), L.ptr(st)))
+        with self.device_order():
+            L.check(self.lib.bpm_run_batch_dev(self.h, L.ptr(isl), B, byref(q), int(n_intervals), L.ptr(m), n,
+                                               L.ptr(sw), L.ptr(tsw), L.ptr(st)))
         return dict(m=m, switched=sw.bool(), t_sw=tsw, status=st)
 
     def run_plain(self, islands, params, n_intervals, map_id=-1):
@@ -156,13 +190,31 @@ class Context:
                                        L.ptr(tsw), L.ptr(st), byref(ms)))
         return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st, device_ms=ms.value)
 
-    def llg_advance_noalloc(self, islands, params, n_intervals, m_dev, mz_dev=None, map_id=-1):
-        """FP32 advance with no device allocation (bpm_llg_advance_noalloc):
-        m_dev is a device tensor [B][3][ld] updated in place on the context stream."""
+    def run_plain_f64(self, islands, params, n_intervals, map_id=-1):
+        """One island per launch with every step in FP64 (bpm_run_plain_f64; the meshes
+        must be uploaded with keep_f64=True); returns results (m float64) and device ms."""
         isl = island_array(islands)
         q = run_params(params, L.PREC_FP32, map_id)
-        L.check(self.lib.bpm_llg_advance_noalloc(self.h, L.ptr(isl), len(isl), byref(q), int(n_intervals),
-                                                 L.ptr(m_dev), int(m_dev.shape[-1]), L.ptr(mz_dev)))
+        n = max(self.mesh_info(int(mid))["n_nodes"] for mid in np.unique(isl["mesh_id"]))
+        B = len(isl)
+        m = np.zeros((B, 3, n), np.float64)
+        sw = np.zeros(B, np.uint8)
+        tsw = np.zeros(B, np.float64)
+        st = np.zeros(B, np.int32)
+        ms = c_double()
+        L.check(self.lib.bpm_run_plain_f64(self.h, L.ptr(isl), B, byref(q), int(n_intervals), L.ptr(m), n,
+                                           L.ptr(sw), L.ptr(tsw), L.ptr(st), byref(ms)))
+        return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st, device_ms=ms.value)
+
+    def llg_advance_noalloc(self, islands, params, n_intervals, m_dev, mz_dev=None, map_id=-1):
+        """FP32 advance with no device allocation (bpm_llg_advance_noalloc):
+        m_dev is a device tensor [B][3][ld] updated in place, ordered against
+        torch's current stream."""
+        isl = island_array(islands)
+        q = run_params(params, L.PREC_FP32, map_id)
+        with self.device_order():
+            L.check(self.lib.bpm_llg_advance_noalloc(self.h, L.ptr(isl), len(isl), byref(q), int(n_intervals),
+                                                     L.ptr(m_dev), int(m_dev.shape[-1]), L.ptr(mz_dev)))
 
     def neb(self, islands, n_images: int, max_iters: int, step: float, spring: float, climb_after: int = -1,
             precision: int = L.PREC_BF16X3, map_id: int = -1, head_x_nm: float = 0.0, uniform_T=(0.0, 0.0, 0.0),
@@ -243,7 +295,8 @@ class Surrogate:
         else:
             X = np.ascontiguousarray(X, np.float32)
             P = np.zeros((X.shape[0], self.n_out), np.float32)
-        L.check(self.lib.bpm_surrogate_infer(self.ctx.h, self.sid, L.ptr(X), X.shape[0], L.ptr(P), on_dev))
+        with self.ctx.device_order() if on_dev else contextlib.nullcontext():
+            L.check(self.lib.bpm_surrogate_infer(self.ctx.h, self.sid, L.ptr(X), X.shape[0], L.ptr(P), on_dev))
         return P
 
     def screen(self, X, n_designs: int, n_jitter: int):
@@ -261,7 +314,9 @@ class Surrogate:
         else:
             X = np.ascontiguousarray(X, np.float32)
             R = np.zeros((n_designs, self.n_out), np.float64)
-        L.check(self.lib.bpm_surrogate_screen(self.ctx.h, self.sid, L.ptr(X), n_designs, n_jitter, L.ptr(R), on_dev))
+        with self.ctx.device_order() if on_dev else contextlib.nullcontext():
+            L.check(self.lib.bpm_surrogate_screen(self.ctx.h, self.sid, L.ptr(X), n_designs, n_jitter, L.ptr(R),
+                                                  on_dev))
         return R
 
     def save(self, path: str):
@@ -305,7 +360,8 @@ class Batch:
         ld = self.n if m is None else int(m.shape[-1])
         if m is not None and not on_dev:
             m = np.ascontiguousarray(m, np.float32)
-        L.check(self.lib.bpm_batch_set_state(self.h, L.ptr(m), ld, float(t0_ps), on_dev))
+        with self.ctx.device_order() if on_dev else contextlib.nullcontext():
+            L.check(self.lib.bpm_batch_set_state(self.h, L.ptr(m), ld, float(t0_ps), on_dev))
 
     def advance(self, n_intervals: int):
         L.check(self.lib.bpm_batch_advance(self.h, int(n_intervals)))
@@ -322,8 +378,9 @@ class Batch:
     def read_device(self, m, switched, t_sw, status, mz):
         """Stream-ordered read into device tensors (any may be None)."""
         ld = self.n if m is None else int(m.shape[-1])
-        L.check(self.lib.bpm_batch_read(self.h, L.ptr(m), ld, L.ptr(switched), L.ptr(t_sw), L.ptr(status),
-                                        L.ptr(mz), 1))
+        with self.ctx.device_order():
+            L.check(self.lib.bpm_batch_read(self.h, L.ptr(m), ld, L.ptr(switched), L.ptr(t_sw), L.ptr(status),
+                                            L.ptr(mz), 1))
 
     def field(self, t_ps: float, term_mask: int) -> np.ndarray:
         out = np.zeros((self.B, 3, self.n), np.float32)
@@ -400,25 +457,9 @@ class Batch:
         return t.value
 
 
-def field_bound(ctx: "Context", mesh_id: int, islands, params, head_map=None) -> float:
-    """Upper bound of |B_eff| (T) for a batch: exchange lambda_max (power iteration
-    on the GPU) scaled by the smallest Ms jitter, plus the anisotropy, demag,
-    head, uniform and per-island field bounds."""
-    info = ctx.mesh_info(mesh_id)
-    Ms = ctx.get_operator(mesh_id, L.OP_NODAL_MS_F64)
-    Ku = ctx.get_operator(mesh_id, L.OP_NODAL_KU_F64)
-    Ms_s = np.asarray(islands.Ms_scale, np.float64)
-    Ku_s = np.asarray(islands.Ku_scale, np.float64)
-    b = info["exchange_lambda_max_T"] / Ms_s.min()
-    b += float(np.max(2.0 * Ku / Ms) * np.max(Ku_s / Ms_s))
-    b += 4e-7 * math.pi * float(Ms.max() * Ms_s.max())
-    if head_map is not None and getattr(params, "use_map", True):
-        b += float(np.max(np.linalg.norm(head_map.B_T, axis=-1)))
-    b += float(np.linalg.norm(params.uniform_T)) + float(np.max(np.linalg.norm(islands.Hext_T, axis=1)))
-    return b
-
-
-def stable_substeps(field_bound_T: float, dt_ps: float, alpha: float, courant: float = 0.5) -> int:
-    """Integrator steps per output interval such that gamma/(1+alpha^2) B dt/k <= courant."""
-    gp = 1.76085963023e-1 / (1.0 + alpha * alpha)
-    return max(1, int(math.ceil(gp * field_bound_T * dt_ps / courant)))
+def substeps_for_bound(field_bound_T: float, dt_ps: float, alpha: float) -> int:
+    """The library's step rule (bpm_substeps_for_bound): the smallest k with
+    gamma/(1+alpha^2) B dt / k <= 1/2.  Host arithmetic; needs no GPU."""
+    k = c_int32()
+    L.check(L.load().bpm_substeps_for_bound(float(field_bound_T), float(dt_ps), float(alpha), byref(k)))
+    return k.value

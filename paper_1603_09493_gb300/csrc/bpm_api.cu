@@ -19,6 +19,89 @@ void set_error(const char* fmt, ...) {
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Heun's explicit step is stable on the fastest precession mode when
+// gamma/(1+alpha^2) |B| h <= 1/2; k is the smallest step count per output
+// interval that keeps h = dt/k there for the largest field the run can see.
+static int substeps_for_bound(double bound_T, double dt_ps, double alpha) {
+    const double gp = kGammaPs / (1.0 + alpha * alpha);
+    const double k = std::ceil(gp * bound_T * dt_ps / 0.5);
+    return k < 1.0 ? 1 : (int)k;
+}
+
+int stable_substeps(bpm_ctx* ctx, const bpm_island* isl, int B, const bpm_run_params* p, int* k, double* bound) {
+    if (!ctx || !isl || !p || B < 1 || !(p->dt_ps > 0) || !(p->alpha >= 0)) {
+        set_error("bad step-count arguments (B >= 1, dt > 0, alpha >= 0)");
+        return BPM_ERR_ARG;
+    }
+    const HeadMap* H = nullptr;
+    if (p->map_id >= 0) {
+        if (p->map_id >= (int)ctx->maps.size() || !ctx->maps[p->map_id]) {
+            set_error("unknown head map id %d", p->map_id);
+            return BPM_ERR_ARG;
+        }
+        H = ctx->maps[p->map_id];
+    }
+    const double uni = std::sqrt((double)p->uniform_T[0] * p->uniform_T[0] + (double)p->uniform_T[1] * p->uniform_T[1] +
+                                 (double)p->uniform_T[2] * p->uniform_T[2]);
+    // the bound of each mesh over its own islands; the run's bound is the largest
+    struct Ext {
+        int mesh;
+        double ms_min, ms_max, kr_max, hext_max;
+    };
+    std::vector<Ext> ext;
+    for (int b = 0; b < B; ++b) {
+        const bpm_island& I = isl[b];
+        const int mid = I.mesh_id;
+        if (mid < 0 || mid >= (int)ctx->meshes.size() || !ctx->meshes[mid]) {
+            set_error("island %d: unknown mesh id %d", b, mid);
+            return BPM_ERR_ARG;
+        }
+        if (!(I.Ms_scale > 0) || !(I.Ku_scale >= 0)) {
+            set_error("island %d: Ms_scale must be > 0 and Ku_scale >= 0", b);
+            return BPM_ERR_ARG;
+        }
+        const double ms = I.Ms_scale, kr = (double)I.Ku_scale / (double)I.Ms_scale;
+        const double he = std::sqrt((double)I.Hext_T[0] * I.Hext_T[0] + (double)I.Hext_T[1] * I.Hext_T[1] +
+                                    (double)I.Hext_T[2] * I.Hext_T[2]);
+        size_t g = 0;
+        while (g < ext.size() && ext[g].mesh != mid) ++g;
+        if (g == ext.size()) {
+            ext.push_back(Ext{mid, ms, ms, kr, he});
+            continue;
+        }
+        Ext& e = ext[g];
+        e.ms_min = std::min(e.ms_min, ms);
+        e.ms_max = std::max(e.ms_max, ms);
+        e.kr_max = std::max(e.kr_max, kr);
+        e.hext_max = std::max(e.hext_max, he);
+    }
+    double best = 0;
+    for (const Ext& e : ext) {
+        const Mesh* M = ctx->meshes[e.mesh];
+        double b = M->info.exchange_lambda_max_T / e.ms_min;   // exchange: lambda_max of S, divided by the Ms factor
+        b += M->an_max * e.kr_max;                             // anisotropy 2 Ku/Ms x Ku_s/Ms_s
+        b += kMu0 * M->ms_max * e.ms_max;                      // demag: |mu0 H_d| <= mu0 Ms
+        if (H) b += H->max_norm;                               // head map
+        b += uni + e.hext_max;                                 // uniform and per-island constant fields
+        best = std::max(best, b);
+    }
+    *k = substeps_for_bound(best, p->dt_ps, p->alpha);
+    if (bound) *bound = best;
+    return BPM_OK;
+}
+
+int run_substeps(bpm_ctx* ctx, const bpm_island* isl, int B, const bpm_run_params* p, int* k) {
+    if (p->substeps < 0) {
+        set_error("substeps %d < 0 (0 picks the stable count)", p->substeps);
+        return BPM_ERR_ARG;
+    }
+    if (p->substeps > 0) {
+        *k = p->substeps;
+        return BPM_OK;
+    }
+    return stable_substeps(ctx, isl, B, p, k, nullptr);
+}
+
 }  // namespace bpm
 
 using namespace bpm;
@@ -267,6 +350,36 @@ int dalloc(T** p, size_t count) {
 extern "C" {
 
 const char* bpm_last_error(void) { return g_err; }
+
+int bpm_substeps_for_bound(double field_bound_T, double dt_ps, double alpha, int32_t* substeps) {
+    if (!substeps || !(field_bound_T >= 0) || !(dt_ps > 0) || !(alpha >= 0)) {
+        set_error("bad step-rule arguments (bound >= 0, dt > 0, alpha >= 0, substeps not null)");
+        return BPM_ERR_ARG;
+    }
+    *substeps = substeps_for_bound(field_bound_T, dt_ps, alpha);
+    return BPM_OK;
+}
+
+int bpm_stable_substeps(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_run_params* p, int32_t* substeps,
+                        double* field_bound_T) {
+    if (!substeps) {
+        set_error("substeps is null");
+        return BPM_ERR_ARG;
+    }
+    int k = 0;
+    BPM_TRY(stable_substeps(ctx, isl, B, p, &k, field_bound_T));
+    *substeps = k;
+    return BPM_OK;
+}
+
+int bpm_context_stream(bpm_ctx* ctx, void** cuda_stream) {
+    if (!ctx || !cuda_stream) {
+        set_error("null argument");
+        return BPM_ERR_ARG;
+    }
+    *cuda_stream = static_cast<void*>(ctx->stream);
+    return BPM_OK;
+}
 const char* bpm_version(void) { return "bpmllg 0.1 (sm_103a)"; }
 
 int bpm_create(bpm_ctx** out, int device, void* cuda_stream) {
@@ -429,8 +542,14 @@ int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, i
     BPM_TRY(ensure_device(ctx));
     size_t N = (size_t)nx * ny * nz;
     std::vector<float4> v(N);
-    for (size_t k = 0; k < N; ++k) v[k] = make_float4(B_T[3 * k], B_T[3 * k + 1], B_T[3 * k + 2], 0.f);
+    double max_norm = 0;
+    for (size_t k = 0; k < N; ++k) {
+        v[k] = make_float4(B_T[3 * k], B_T[3 * k + 1], B_T[3 * k + 2], 0.f);
+        const double bx = B_T[3 * k], by = B_T[3 * k + 1], bz = B_T[3 * k + 2];
+        max_norm = std::max(max_norm, std::sqrt(bx * bx + by * by + bz * bz));
+    }
     HeadMap* H = new HeadMap();
+    H->max_norm = max_norm;
     H->nx = nx;
     H->ny = ny;
     H->nz = nz;
@@ -478,10 +597,12 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         return BPM_ERR_ARG;
     }
     *out = nullptr;
-    if (p->substeps < 1 || !(p->dt_ps > 0) || p->precision < 0 || p->precision > 3) {
-        set_error("bad run parameters (substeps >= 1, dt > 0, precision 0..3)");
+    if (p->substeps < 0 || !(p->dt_ps > 0) || p->precision < 0 || p->precision > 3) {
+        set_error("bad run parameters (substeps >= 0, dt > 0, precision 0..3)");
         return BPM_ERR_ARG;
     }
+    int k_steps = 0;
+    BPM_TRY(run_substeps(ctx, isl, B, p, &k_steps));
     HeadMap* H = nullptr;
     if (p->map_id >= 0) {
         if (p->map_id >= (int)ctx->maps.size()) {
@@ -514,6 +635,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
     bt->map = H;
     bt->B = B;
     bt->p = *p;
+    bt->p.substeps = k_steps;
     bt->t0 = p->t0_ps;
     int r = BPM_OK;
     auto chk = [&](int rr) {
@@ -597,8 +719,8 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         a.status = g.status;
         a.interval = bt->interval;
         a.t0 = p->t0_ps;
-        a.k = p->substeps;
-        a.h = p->dt_ps / p->substeps;
+        a.k = k_steps;
+        a.h = p->dt_ps / k_steps;
         a.alpha = (float)p->alpha;
         a.gp = (float)(kGammaPs / (1.0 + p->alpha * p->alpha));
         a.rise = (float)p->rise_ps;

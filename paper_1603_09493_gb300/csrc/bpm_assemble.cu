@@ -165,6 +165,16 @@ __global__ void k_exchange_values(int n, const int* __restrict__ rowptr, const i
     for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) c[e] = (col[e] == i) ? 0.f : (float)(s * KA[e]);
 }
 
+// the same values in FP64, kept for the plain FP64 form
+__global__ void k_exchange_values64(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                    const double* __restrict__ KA, const double* __restrict__ V,
+                                    const double* __restrict__ Ms, double* __restrict__ c) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = -2.0e18 / (Ms[i] * V[i]);
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) c[e] = (col[e] == i) ? 0.0 : s * KA[e];
+}
+
 __device__ double block_sum(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -596,6 +606,11 @@ void free_mesh(Mesh* M) {
     cudaFree(M->Nhi);
     cudaFree(M->Nlo);
     cudaFree(M->N64);
+    cudaFree(M->csr_rowptr);
+    cudaFree(M->csr_col);
+    cudaFree(M->csr_c64);
+    cudaFree(M->node64);
+    cudaFree(M->mat64);
     delete M;
 }
 
@@ -750,6 +765,12 @@ int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets_
     float* d_c;
     BPM_TRY(pool.alloc(&d_c, nnz));
     k_exchange_values<<<(n + T - 1) / T, T, 0, st>>>(n, d_rowptr, d_col, d_KA, d_V, d_Ms, d_c);
+    BPM_CK(cudaMalloc(&M->csr_rowptr, (n + 1) * sizeof(int)));
+    BPM_CK(cudaMalloc(&M->csr_col, nnz * sizeof(int)));
+    BPM_CK(cudaMalloc(&M->csr_c64, nnz * sizeof(double)));
+    BPM_CK(cudaMemcpyAsync(M->csr_rowptr, d_rowptr, (n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    BPM_CK(cudaMemcpyAsync(M->csr_col, d_col, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    k_exchange_values64<<<(n + T - 1) / T, T, 0, st>>>(n, d_rowptr, d_col, d_KA, d_V, d_Ms, M->csr_c64);
     double *d_px, *d_py, *d_lam;
     BPM_TRY(pool.alloc(&d_px, n));
     BPM_TRY(pool.alloc(&d_py, n));
@@ -885,6 +906,16 @@ int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets_
         const int j = ent[k].x;
         ent_il[k] = make_int2(4 * ((j >> 5) * 96 * kIlIslands + (j & 31)), ent[k].y);
     }
+    std::vector<NodeF64> node64(n);
+    std::vector<double2> mat64(n);
+    for (int i = 0; i < n; ++i) {
+        node64[i] = NodeF64{xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], M->V[i] / Vsum};
+        mat64[i] = make_double2(2.0 * M->Ku[i] / M->Ms[i], M->Ms[i]);
+    }
+    BPM_CK(cudaMalloc(&M->node64, n * sizeof(NodeF64)));
+    BPM_CK(cudaMalloc(&M->mat64, n * sizeof(double2)));
+    BPM_CK(cudaMemcpy(M->node64, node64.data(), n * sizeof(NodeF64), cudaMemcpyHostToDevice));
+    BPM_CK(cudaMemcpy(M->mat64, mat64.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
     BPM_CK(cudaMalloc(&M->node_pos, np * sizeof(float4)));
     BPM_CK(cudaMalloc(&M->node_mat, np * sizeof(float4)));
     BPM_CK(cudaMalloc(&M->sell_off, off.size() * sizeof(int)));
@@ -910,6 +941,8 @@ int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets_
     I.volume_nm3 = Vsum;
     I.exchange_lambda_max_T = lam;
     I.field_bound_T = lam + an_max + kMu0 * ms_max;
+    M->an_max = an_max;
+    M->ms_max = ms_max;
     I.cg_residual_neumann = res1;
     I.cg_residual_dirichlet = res2;
     return BPM_OK;

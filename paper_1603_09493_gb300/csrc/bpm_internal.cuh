@@ -44,6 +44,11 @@ void set_error(const char* fmt, ...);
 // so that the three components of both islands sit at fixed distances from node j's word.
 constexpr int kIlIslands = 2;
 
+// Position (nm) and lumped volume weight V_i / sum V of one node, FP64.
+struct NodeF64 {
+    double x, y, z, w;
+};
+
 // Device-resident operators of one island mesh.
 struct Mesh {
     int n = 0, n_pad = 0, n_tets = 0, nb = 0, nnz = 0;
@@ -67,10 +72,19 @@ struct Mesh {
     __nv_bfloat16* Nhi = nullptr; // [K][K]
     __nv_bfloat16* Nlo = nullptr; // [K][K]
     double* N64 = nullptr;        // [3n][3n] compact, H = -N M (only with BPM_MESH_KEEP_F64)
+    // FP64 copies for the plain FP64 form: exchange CSR in difference form, c_ij (T per unit m,
+    // c_ii = 0), and per node (x, y, z, V_i / sum V) and (2 Ku_i / Ms_i in T, Ms_i in A/m)
+    int* csr_rowptr = nullptr;    // [n + 1]
+    int* csr_col = nullptr;       // [nnz]
+    double* csr_c64 = nullptr;    // [nnz]
+    NodeF64* node64 = nullptr;    // [n]
+    double2* mat64 = nullptr;     // [n]
     // host copies for export
     std::vector<int> rowptr, col; // CSR pattern incl. diagonal
     std::vector<float> exch_val;  // c_ij per CSR entry (0 on the diagonal)
     std::vector<double> V, Ms, Ku;
+    double an_max = 0;            // max_i 2 Ku_i / Ms_i (T)
+    double ms_max = 0;            // max_i Ms_i (A/m)
     bpm_mesh_info info{};
     int K() const { return k_pad; }
 };
@@ -82,6 +96,7 @@ struct HeadMap {
     int nx = 0, ny = 0, nz = 0;
     float h = 1.f;
     float origin[3] = {0, 0, 0};
+    double max_norm = 0;          // largest |B| of a voxel (T)
 };
 
 struct Mlp;
@@ -104,6 +119,11 @@ struct bpm_ctx {
 };
 
 namespace bpm {
+
+// Integrator step count of a run (bpm_stable_substeps): *k (>= 1) and the field bound (T)
+int stable_substeps(bpm_ctx* ctx, const bpm_island* isl, int B, const bpm_run_params* p, int* k, double* bound);
+// Heun steps of a run: p->substeps, or the stable count when p->substeps is 0
+int run_substeps(bpm_ctx* ctx, const bpm_island* isl, int B, const bpm_run_params* p, int* k);
 
 // assembly (bpm_assemble.cu)
 int assemble_mesh(bpm_ctx* ctx, Mesh* M, const double* xyz, const int32_t* tets, int32_t n_tets,

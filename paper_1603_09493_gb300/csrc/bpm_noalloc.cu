@@ -77,10 +77,12 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
                   p->precision);
         return BPM_ERR_ARG;
     }
-    if (p->substeps < 1 || !(p->dt_ps > 0)) {
-        set_error("bad run parameters (substeps >= 1, dt > 0)");
+    if (p->substeps < 0 || !(p->dt_ps > 0)) {
+        set_error("bad run parameters (substeps >= 0, dt > 0)");
         return BPM_ERR_ARG;
     }
+    int k_steps = 0;
+    BPM_TRY(run_substeps(ctx, isl, B, p, &k_steps));
     const HeadMap* H = nullptr;
     if (p->map_id >= 0) {
         if (p->map_id >= (int)ctx->maps.size()) {
@@ -182,8 +184,8 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
     long long* interval = reinterpret_cast<long long*>(s8 + o_it);
     a.interval = interval;
     a.t0 = p->t0_ps;
-    a.k = p->substeps;
-    a.h = p->dt_ps / p->substeps;
+    a.k = k_steps;
+    a.h = p->dt_ps / k_steps;
     a.alpha = (float)p->alpha;
     a.gp = (float)(kGammaPs / (1.0 + p->alpha * p->alpha));
     a.rise = (float)p->rise_ps;
@@ -193,7 +195,7 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
     a.mask = p->term_mask;
     launch_init(a, s);
     for (int it = 0; it < n_intervals; ++it) {
-        for (int j = 0; j < p->substeps; ++j) {
+        for (int j = 0; j < k_steps; ++j) {
             BPM_TRY(gemm_f32_nt(s, B, K, K, a.A32, K, M->N32, K, hd, K));
             launch_stage1(a, j, s);
             BPM_TRY(gemm_f32_nt(s, B, K, K, a.A32, K, M->N32, K, hd, K));

@@ -99,7 +99,7 @@ def run_params(t_end_ps: float = 100.0) -> synth.RunParams:
 def llg_outcomes(ctx: api.Context, mesh_id: int, p: synth.RunParams, target, adjacent) -> np.ndarray:
     """LLG labels [N][2]: (target switched, adjacent island flipped), one batch."""
     isl = synth.Islands.concat([target, adjacent])
-    p.substeps = api.stable_substeps(api.field_bound(ctx, mesh_id, isl, p), p.dt_ps, p.alpha)
+    p.substeps = ctx.stable_substeps(isl, p)[0]
     out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_BF16X3)
     if np.any(out["status"] != 0):
         raise RuntimeError("an island of the verification batch reported a failure")

@@ -1,0 +1,181 @@
+"""Write the FP64 oracle's results for the headline parity tests (test infrastructure).
+
+Only the oracle (oracle/) and the seeded input generators (synth) run here; no
+value comes from the CUDA path.  The oracle needs about an hour of host time
+for these runs, more than a test may take, so its results are stored:
+
+  census      tests/golden/census_first_100ps.npz
+              64 islands sampled from the 4096-island census workload (the
+              bench's: 1547-node mesh, jitter seed 1, 64x64x16 head map moving
+              at 20 m/s from x0 = -10 nm, 100 ps rise, alpha 0.1), integrated
+              over the first 100 ps with the workload's step count k; the
+              volume-averaged m_z after every 0.1 ps interval, and every
+              node's m every 10 ps (stored as int16, m = q / 32767, a rounding
+              of at most 1.6e-5).
+  outcomes    tests/golden/outcome_census_209.npz
+              1024 jittered islands of the 209-node mesh written by the moving
+              head (Sec. II.C recording simulation: the head field plus a
+              constant field H_ext opposing it, spread over the islands so that
+              a real fraction of them switches); the switch flag, first
+              crossing time and final volume-averaged m_z of every island.
+
+  python tests/golden/make_headline_golden.py census|outcomes [--workers N]
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+GOLDEN = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# census workload
+CENSUS_B = 4096
+CENSUS_SAMPLES = 64
+CENSUS_INTERVALS = 1000          # 100 ps at 0.1 ps
+CENSUS_SNAPSHOT_EVERY = 100      # full state every 10 ps
+
+# outcome census
+OUTCOME_B = 1024
+OUTCOME_SEED = 5
+OUTCOME_T_END_PS = 500.0
+OUTCOME_X0_NM = -4.0
+OUTCOME_HEXT_MAX_T = 0.3
+
+
+def census_params():
+    from paper_1603_09493_gb300 import synth
+    return synth.RunParams(dt_ps=0.1, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=-10.0, use_map=True,
+                           t_end_ps=CENSUS_INTERVALS * 0.1)
+
+
+def census_sample_index() -> np.ndarray:
+    return np.round(np.linspace(0, CENSUS_B - 1, CENSUS_SAMPLES)).astype(np.int64)
+
+
+def head_direction() -> np.ndarray:
+    """Unit direction of the synthetic head field (under the pole): (0, sin 25, -cos 25)."""
+    th = math.radians(25.0)
+    return np.array([0.0, math.sin(th), -math.cos(th)])
+
+
+def outcome_islands(mesh_id: int = 0):
+    """1024 jittered islands; island b carries H_ext = -(b / B) * 0.3 T along the head
+    field direction (the Sec. II.C field that opposes writing the target bit)."""
+    from paper_1603_09493_gb300 import synth
+    isl = synth.jittered_islands(OUTCOME_B, seed=OUTCOME_SEED, mesh_id=mesh_id)
+    mag = OUTCOME_HEXT_MAX_T * np.arange(OUTCOME_B) / OUTCOME_B
+    isl.Hext_T[:] = (-mag[:, None] * head_direction()[None, :]).astype(np.float32)
+    return isl
+
+
+def outcome_params():
+    from paper_1603_09493_gb300 import synth
+    return synth.RunParams(dt_ps=0.1, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=OUTCOME_X0_NM, use_map=True,
+                           t_end_ps=OUTCOME_T_END_PS)
+
+
+def _census_chunk(args):
+    idx, k = args
+    from oracle import fem, llg
+    from paper_1603_09493_gb300 import synth
+    mesh = synth.census_island_mesh()
+    mats = synth.ecc_materials()
+    hm = synth.synthetic_head_map()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    p = census_params()
+    p.substeps = k
+    b = llg.Batch(ops, synth.jittered_islands(CENSUS_B, seed=1).subset(idx), p, head_map=hm)
+    mz, steps = [], [0]
+
+    def on_step(m, t):
+        steps[0] += 1
+        if steps[0] % k == 0:
+            mz.append(b.mz_avg(m))
+
+    r = b.run(sample_every=CENSUS_SNAPSHOT_EVERY, on_step=on_step)
+    return np.array(mz), np.array(r["samples"])
+
+
+def _outcome_chunk(args):
+    lo, hi, k = args
+    from oracle import fem, llg
+    from paper_1603_09493_gb300 import synth
+    mesh = synth.small_island_mesh()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, synth.ecc_materials())
+    p = outcome_params()
+    p.substeps = k
+    b = llg.Batch(ops, outcome_islands().subset(np.arange(lo, hi)), p, head_map=synth.synthetic_head_map())
+    r = b.run()
+    return r["switched"], r["t_sw"], r["mz"], r["status"]
+
+
+def _pool(workers):
+    # one BLAS thread per worker process; spawned, so that no parent state is forked
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["MKL_NUM_THREADS"] = "1"
+    return mp.get_context("spawn").Pool(workers)
+
+
+def make_census(workers: int):
+    from oracle import fem, llg
+    from paper_1603_09493_gb300 import synth
+    mesh = synth.census_island_mesh()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, synth.ecc_materials(), with_demag=False)
+    p = census_params()
+    k = llg.stable_substeps(llg.Batch(ops, synth.jittered_islands(CENSUS_B, seed=1), p,
+                                      head_map=synth.synthetic_head_map(), demag=np.zeros((1, 1))))
+    idx = census_sample_index()
+    chunks = np.array_split(idx, workers)
+    t = time.time()
+    with _pool(workers) as pool:
+        res = pool.map(_census_chunk, [(c, k) for c in chunks])
+    mz = np.concatenate([r[0] for r in res], axis=1)                  # [intervals][samples]
+    snaps = np.concatenate([r[1] for r in res], axis=1)               # [snapshots][samples][n][3]
+    q = np.round(snaps * 32767.0).astype(np.int16)
+    isl = synth.jittered_islands(CENSUS_B, seed=1).subset(idx)
+    out = os.path.join(GOLDEN, "census_first_100ps.npz")
+    np.savez_compressed(out, k=k, index=idx, mz=mz, m_q=q, snapshot_every=CENSUS_SNAPSHOT_EVERY,
+                        Ms_scale=isl.Ms_scale, Ku_scale=isl.Ku_scale, u=isl.u, pos_nm=isl.pos_nm,
+                        n_nodes=mesh.n_nodes, xyz_sum=float(mesh.xyz_nm.sum()))
+    print(f"census: k={k}, {len(idx)} islands, {mz.shape[0]} intervals, {time.time() - t:.0f} s -> {out}")
+
+
+def make_outcomes(workers: int):
+    from oracle import fem, llg
+    from paper_1603_09493_gb300 import synth
+    mesh = synth.small_island_mesh()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, synth.ecc_materials(), with_demag=False)
+    p = outcome_params()
+    isl = outcome_islands()
+    k = llg.stable_substeps(llg.Batch(ops, isl, p, head_map=synth.synthetic_head_map(), demag=np.zeros((1, 1))))
+    bounds = np.linspace(0, OUTCOME_B, 4 * workers + 1).astype(int)
+    t = time.time()
+    with _pool(workers) as pool:
+        res = pool.map(_outcome_chunk, [(bounds[i], bounds[i + 1], k) for i in range(len(bounds) - 1)])
+    sw = np.concatenate([r[0] for r in res])
+    tsw = np.concatenate([r[1] for r in res])
+    mz = np.concatenate([r[2] for r in res])
+    st = np.concatenate([r[3] for r in res])
+    out = os.path.join(GOLDEN, "outcome_census_209.npz")
+    np.savez_compressed(out, k=k, switched=sw, t_sw=tsw, mz=mz, status=st, Ms_scale=isl.Ms_scale,
+                        Ku_scale=isl.Ku_scale, u=isl.u, pos_nm=isl.pos_nm, Hext_T=isl.Hext_T,
+                        t_end_ps=OUTCOME_T_END_PS)
+    print(f"outcomes: k={k}, {sw.sum()} of {sw.size} switched, {time.time() - t:.0f} s -> {out}")
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["census", "outcomes"])
+    ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
+    a = ap.parse_args()
+    (make_census if a.what == "census" else make_outcomes)(a.workers)

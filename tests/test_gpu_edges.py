@@ -96,8 +96,7 @@ def test_largest_mesh(ctx):
             print(f"largest mesh, term {term}: rel err {err:.2e}")
             assert err <= 2e-5
     # every term on, a ragged batch of 130 islands, a few intervals
-    bound = api.field_bound(ctx, mid, isl, p, hm)
-    p.substeps = api.stable_substeps(bound, p.dt_ps, p.alpha)
+    p.substeps = ctx.stable_substeps(isl, p, hid)[0]
     out = ctx.run_batch(isl, p, 3, precision=L.PREC_BF16X3, map_id=hid)
     assert np.all(out["status"] == 0)
     nrm = np.linalg.norm(out["m"][:, :, :mesh.n_nodes], axis=1)
@@ -178,7 +177,7 @@ def test_stoner_wohlfarth_switching_field_at_45_degrees(ctx):
                                   for h in hs], np.float32))
     p = synth.RunParams(dt_ps=1.0, t_end_ps=600.0, alpha=1.0, rise_ps=0.0, use_map=False,
                         term_mask=L.TERM_EXCHANGE | L.TERM_ANISOTROPY | L.TERM_UNIFORM)
-    p.substeps = api.stable_substeps(api.field_bound(ctx, mid, isl, p), p.dt_ps, p.alpha)
+    p.substeps = ctx.stable_substeps(isl, p)[0]
     out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_FP32)
     print("switched", out["switched"], "t_sw", out["t_sw"])
     assert not out["switched"][0] and out["switched"][1]
@@ -191,7 +190,7 @@ def test_device_output_run_matches_the_host_run(ctx):
     isl = synth.jittered_islands(37, seed=8, mesh_id=mid)
     p = synth.RunParams(dt_ps=0.1, t_end_ps=20.0, alpha=0.1, rise_ps=10.0, use_map=True, x0_nm=-2.0,
                         uniform_T=synth.uniform_field(0.6, 165.0))
-    p.substeps = api.stable_substeps(api.field_bound(ctx, mid, isl, p, synth.synthetic_head_map()), p.dt_ps, p.alpha)
+    p.substeps = ctx.stable_substeps(isl, p, hid)[0]
     host = ctx.run_batch(isl, p, p.n_intervals, map_id=hid)
     dev = ctx.run_batch_dev(isl, p, p.n_intervals, map_id=hid)
     assert dev["m"].is_cuda and dev["switched"].is_cuda

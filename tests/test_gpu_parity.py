@@ -181,7 +181,7 @@ def test_census_size_sampled_islands(ctx, headmap):
     B = 4096
     isl = synth.jittered_islands(B, seed=1, mesh_id=mid)
     p = synth.RunParams(dt_ps=0.1, t_end_ps=1.0, alpha=0.1, rise_ps=100.0, use_map=True, x0_nm=-2.0)
-    p.substeps = api.stable_substeps(api.field_bound(ctx, mid, isl, p, hm), p.dt_ps, p.alpha)
+    p.substeps = ctx.stable_substeps(isl, p, hid)[0]
     assert p.substeps == llg.stable_substeps(llg.Batch(ops, isl.subset(np.arange(B)), p, head_map=hm))
     out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_BF16X3, map_id=hid)
     assert np.all(out["status"] == 0)

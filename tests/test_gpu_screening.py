@@ -37,7 +37,7 @@ def test_surrogate_screening_gain():
         p = synth.RunParams(dt_ps=0.1, t_end_ps=100.0, alpha=0.1, rise_ps=0.0, use_map=False)
 
         def label(isl):
-            p.substeps = api.stable_substeps(api.field_bound(ctx, mid, isl, p), p.dt_ps, p.alpha)
+            p.substeps = ctx.stable_substeps(isl, p)[0]
             out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_BF16X3)
             assert np.all(out["status"] == 0)
             return np.stack([out["switched"], (out["t_sw"] > 0) & (out["t_sw"] <= 40.0)], 1).astype(np.float32)

@@ -1,26 +1,58 @@
-"""Host-side rules of the binding (no GPU): the integrator step count is the
-smallest k with gamma/(1 + alpha^2) B dt / k <= 1/2 (the explicit-step bound
-Heun's method needs on the precession frequency); the critical-field search of
-Sec. II.C makes the oracle search's decisions when both see the same outcomes."""
+"""Host-side rules of the library and the binding (no GPU): the integrator step
+count is the smallest k with gamma/(1 + alpha^2) B dt / k <= 1/2 (the
+explicit-step bound Heun's method needs on the precession frequency), computed
+by the library itself (bpm_substeps_for_bound, host arithmetic); the
+critical-field search of Sec. II.C makes the oracle search's decisions when
+both see the same outcomes."""
 import math
+import os
 
 import numpy as np
+import pytest
 
+from paper_1603_09493_gb300 import _lib as L
 from paper_1603_09493_gb300 import api
 
 
-def test_stable_substeps_is_the_smallest_admissible_count():
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(L.LIB_PATH):
+        from paper_1603_09493_gb300 import build
+        build.build()
+    return L.load()
+
+
+def test_library_step_count_is_the_smallest_admissible_count(lib):
     gamma = 1.76085963023e-1                                 # rad / (ps T)
     rng = np.random.default_rng(0)
     for B, dt, alpha in zip(rng.uniform(0.01, 500.0, 200), rng.uniform(0.01, 1.0, 200), rng.uniform(0.0, 1.0, 200)):
-        k = api.stable_substeps(B, dt, alpha)
+        k = api.substeps_for_bound(B, dt, alpha)
         rate = gamma / (1.0 + alpha * alpha) * B * dt
         assert k >= 1 and rate / k <= 0.5 * (1 + 1e-12)
         assert k == 1 or rate / (k - 1) > 0.5
     # the census numbers: 28 steps per 0.1 ps at alpha 0.1 for a bound near 800 T (the exchange spectrum)
-    assert api.stable_substeps(800.0, 0.1, 0.1) == 28
-    assert api.stable_substeps(0.0, 0.1, 0.1) == 1
-    assert api.stable_substeps(1.0, 0.1, 0.0, courant=0.25) == math.ceil(gamma * 0.1 / 0.25)
+    assert api.substeps_for_bound(800.0, 0.1, 0.1) == 28
+    assert api.substeps_for_bound(0.0, 0.1, 0.1) == 1
+    assert api.substeps_for_bound(1.0, 0.1, 0.0) == math.ceil(gamma * 0.1 / 0.5)
+    # the same rule as the oracle's, on the oracle's own bound of a batch
+    from oracle import fem, llg
+    from paper_1603_09493_gb300 import synth
+    mesh = synth.small_island_mesh()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, synth.ecc_materials(), with_demag=False)
+    for seed, alpha in ((1, 0.1), (2, 0.02), (3, 1.0)):
+        isl = synth.jittered_islands(64, seed=seed)
+        p = synth.RunParams(dt_ps=0.1, alpha=alpha, use_map=False, uniform_T=synth.uniform_field(0.5, 170.0))
+        b = llg.Batch(ops, isl, p, demag=np.zeros((1, 1)))
+        assert api.substeps_for_bound(llg.field_bound(b), p.dt_ps, alpha) == llg.stable_substeps(b)
+    # arguments outside the rule's domain are refused
+    k = ctypes_int()
+    for args in ((-1.0, 0.1, 0.1), (1.0, 0.0, 0.1), (1.0, 0.1, -0.5)):
+        assert lib.bpm_substeps_for_bound(*args, k) == L.BPM_ERR_ARG
+
+
+def ctypes_int():
+    import ctypes
+    return ctypes.byref(ctypes.c_int32())
 
 
 def _threshold_rule(isl, role):
