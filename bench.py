@@ -39,9 +39,7 @@ def workload(seed: int = 1):
     mesh = synth.census_island_mesh(seed=seed)
     mats = synth.ecc_materials()
     hm = synth.synthetic_head_map()
-    p = synth.RunParams(dt_ps=DT_PS, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=-10.0, use_map=True,
-                        t_end_ps=DT_PS)
-    return mesh, mats, hm, p
+    return mesh, mats, hm, synth.census_run_params(t_end_ps=DT_PS)
 
 
 def config_dict(mesh, k, precision, B, n_gpus):
@@ -131,46 +129,89 @@ def gemm_traffic(prec, B, n):
     return NCU_GEMM_TRAFFIC.get((int(prec), int(B), int(n)))
 
 
-_ORACLE_OPS = {}
+# ---------------------------------------------------------------------------
+# The FP64 oracle on the host cores: one spawned worker process per core, each
+# with one BLAS thread and its own copy of the census mesh operators, each
+# integrating its own islands.
+
+_WORKER = {}
 
 
-def oracle_ops(mesh, mats):
-    """The oracle's operators of a mesh, built once per run (about a minute for the census mesh)."""
+def _oracle_worker_init(barrier):
     from oracle import fem
-    key = (id(mesh), id(mats))
-    if key not in _ORACLE_OPS:
-        _ORACLE_OPS[key] = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
-    return _ORACLE_OPS[key]
+    mesh, mats, hm, _ = workload()
+    _WORKER["ops"] = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    _WORKER["hm"] = hm
+    barrier.wait()
 
 
-def run_oracle_sample(islands, n_intervals, k, mesh, mats, hm, p):
-    """Time the FP64 oracle on a bounded sample; returns seconds."""
+def _oracle_worker_run(task):
+    """task = (islands, params, m0 or None) -> final m of the islands."""
     from oracle import llg
-    ops = oracle_ops(mesh, mats)
-    pp = type(p)(**{**p.__dict__})
-    pp.substeps = k
-    pp.t_end_ps = pp.t0_ps + n_intervals * pp.dt_ps
-    b = llg.Batch(ops, islands, pp, head_map=hm)
-    t = time.perf_counter()
-    b.run()
-    return time.perf_counter() - t
+    isl, p, m0 = task
+    return llg.Batch(_WORKER["ops"], isl, p, head_map=_WORKER["hm"]).run(m0)["m"]
 
 
-def cpu_baseline(mesh, mats, hm, p, k, target_s=15.0):
+class OraclePool:
+    """Worker processes with the census workload's oracle operators built; the
+    constructor returns once every worker holds them, so that timing starts
+    after the set-up."""
+
+    def __init__(self, workers: int):
+        import multiprocessing as mp
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(workers + 1)
+        self.workers = workers
+        self.pool = ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(barrier,))
+        barrier.wait()
+
+    def run(self, tasks):
+        return self.pool.map(_oracle_worker_run, tasks, chunksize=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def oracle_step_count(p):
+    """The workload's integrator step count by the oracle's own rule (over all its islands)."""
+    from oracle import fem, llg
     from paper_1603_09493_gb300 import synth
-    isl = synth.jittered_islands(16, seed=1)
-    t1 = run_oracle_sample(isl, 1, k, mesh, mats, hm, p)
-    nint = int(max(1, min(40, round(target_s / max(t1, 1e-3)))))
-    t = run_oracle_sample(isl, nint, k, mesh, mats, hm, p)
-    value = len(isl) * nint * DT_PS * 1e-3 / t
-    return {"value": value, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"{len(isl)} islands x {nint} intervals ({nint * k} Heun steps) of the same workload, "
-                      f"numpy FP64, {t:.1f} s"}
+    mesh, mats, hm, _ = workload()
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats, with_demag=False)
+    return llg.stable_substeps(llg.Batch(ops, synth.jittered_islands(B_ISLANDS, seed=1), p, head_map=hm,
+                                         demag=np.zeros((1, 1))))
 
 
-def stable_k(ctx, hid, isl, p):
-    """The library's integrator step count for this workload (bpm_stable_substeps)."""
-    return ctx.stable_substeps(isl, p, hid)[0]
+def cpu_baseline(p, k, target_s=15.0):
+    """The oracle on all host cores: one island per worker, a bounded number of
+    0.1 ps intervals sized to about target_s seconds."""
+    from paper_1603_09493_gb300 import synth
+    W = host_cores()
+    isl = synth.jittered_islands(W, seed=1)
+    pool = OraclePool(W)
+    try:
+        def run(nint):
+            q = type(p)(**{**p.__dict__})
+            q.substeps, q.t0_ps, q.t_end_ps = k, 0.0, nint * DT_PS
+            t = time.perf_counter()
+            pool.run([(isl.subset([w]), q, None) for w in range(W)])
+            return time.perf_counter() - t
+        t1 = run(1)
+        nint = int(max(1, min(40, round(target_s / max(t1, 1e-3)))))
+        t = run(nint)
+    finally:
+        pool.close()
+    return {"value": W * nint * DT_PS * 1e-3 / t, "unit": UNIT, "cores": W, "kind": "oracle",
+            "workers": f"{W} processes, one per host core, 1 BLAS thread each",
+            "sample": f"{W} islands (one per worker) x {nint} intervals ({nint * k} Heun steps) of the census "
+                      f"workload, numpy FP64, {t:.1f} s"}
 
 
 def measure_plain(ctx, isl, p, hid, prec, n, islands=8, intervals=2):
@@ -184,6 +225,91 @@ def measure_plain(ctx, isl, p, hid, prec, n, islands=8, intervals=2):
             "form": "one island per launch, FP32 GEMV demag streamed from HBM, single-island stage kernels",
             "vs_mixed_max_abs_dm": float(np.abs(plain["m"] - mixed["m"]).max()),
             "same_switch_flags": bool(np.array_equal(plain["switched"], mixed["switched"]))}
+
+
+def measure_plain_f64(ctx, isl, p, hid, mesh, mats, islands=2, intervals=1):
+    """The one-island-per-launch FP64 form (every step in FP64, the FP64 demag
+    matrix streamed per Heun stage) on a few islands of the same workload."""
+    mid = ctx.mesh_upload(mesh, mats, keep_f64=True)
+    sub = isl.subset(np.arange(islands))
+    sub.mesh_id[:] = mid
+    out = ctx.run_plain_f64(sub, p, intervals, map_id=hid)
+    return {"value": islands * intervals * DT_PS * 1e-3 / (out["device_ms"] * 1e-3), "unit": UNIT,
+            "islands": islands, "intervals": intervals,
+            "form": "one island per launch, FP64 GEMV demag with the FP64 operator, FP64 field and Heun kernels"}
+
+
+def measure_parity(ctx, hid):
+    """Switch outcomes of the BF16x3 batch against the FP64 oracle's, stored by
+    tests/golden/make_headline_golden.py: 1024 jittered islands of the 209-node
+    mesh written by the moving head against an opposing field spread over the
+    islands (synth.outcome_census, 300 ps)."""
+    from paper_1603_09493_gb300 import _lib as L
+    from paper_1603_09493_gb300 import synth
+    path = os.path.join(ROOT, "tests", "golden", "outcome_census_209.npz")
+    if not os.path.exists(path):
+        return None
+    ref = np.load(path)
+    mid = ctx.mesh_upload(synth.small_island_mesh(), synth.ecc_materials())
+    isl, p = synth.outcome_census(mesh_id=mid)
+    p.substeps = int(ref["k"])
+    out = ctx.run_batch(isl, p, p.n_intervals, precision=L.PREC_BF16X3, map_id=hid)
+    both = (out["t_sw"] > 0) & (ref["t_sw"] > 0)
+    return {"outcome_agreement": float(np.mean(out["switched"] == ref["switched"])), "islands": len(isl),
+            "switched_fraction": float(np.mean(ref["switched"])),
+            "max_abs_dt_sw_ps": float(np.abs(out["t_sw"][both] - ref["t_sw"][both]).max()) if both.any() else None,
+            "against": "FP64 oracle outcomes (tests/golden/outcome_census_209.npz)",
+            "workload": "1024 jittered islands, 209-node mesh, head map from x0 = -2 nm at 20 m/s, opposing "
+                        "field 0-0.3 T spread over the islands, 300 ps, BF16x3 demag"}
+
+
+def measure_uneven(ctx, hm, hid, realisations=512, steps=3):
+    """Config 2: 16 design variants (518-3906 nodes), `realisations` jittered
+    targets each plus their adjacent-track islands, in one batch (grouped demag
+    GEMM over all mesh groups, one stage launch per occupancy class), for the
+    centered, staggered and shingled layouts; device time of `steps` intervals
+    per layout, and the grouped GEMM's roofline."""
+    from paper_1603_09493_gb300 import _lib as L
+    from paper_1603_09493_gb300 import synth
+    variants = synth.design_variants()
+    mats = synth.ecc_materials()
+    mids = [ctx.mesh_upload(v["mesh"], mats) for v in variants]
+    import torch
+    stream = torch.cuda.ExternalStream(ctx.stream_ptr)
+    pk = peaks()
+    peak, peak_source = gemm_peak(pk)
+    out = {"variants": len(variants), "nodes": [min(v["mesh"].n_nodes for v in variants),
+                                                 max(v["mesh"].n_nodes for v in variants)],
+           "realisations": realisations, "layouts": {}}
+    for layout in ("staggered", "centered", "shingled"):
+        isl, role = synth.uneven_batch(variants, mids, realisations=realisations, seed=2, layout=layout)
+        p = synth.census_run_params()
+        p.substeps = 0
+        k = ctx.stable_substeps(isl, p, hid)[0]
+        with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+            bt.advance(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bt.advance(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            ok = bool(np.all(bt.read()["status"] == 0))
+            entry = {"islands": len(isl), "adjacent_islands": int(np.sum(role == 1)), "heun_steps_per_interval": k,
+                     "value": len(isl) * DT_PS * 1e-3 / (ms * 1e-3), "unit": UNIT, "ms_per_interval": ms,
+                     "launches_per_interval": bt.graph_kernels(), "status_ok": ok}
+            if layout == "staggered":
+                kt = bt.kernel_times(reps=4)
+                flops = sum(6.0 * int(np.sum(isl.mesh_id == mid)) * (3 * v["mesh"].n_nodes) ** 2
+                            for mid, v in zip(mids, variants))
+                entry["roofline"] = {"bound": "tensor", "achieved": flops / (kt["gemm_ms"] * 1e-3) / 1e12,
+                                     "peak": peak, "unit": "TFLOP/s", "peak_source": peak_source,
+                                     "frac": flops / (kt["gemm_ms"] * 1e-3) / 1e12 / peak, "traffic": None,
+                                     "kernel": "grouped demag GEMM over the 16 mesh groups (one launch)"}
+                entry["kernel_ms"] = kt
+        out["layouts"][layout] = entry
+    return out
 
 
 def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400, mesh=None, mats=None):
@@ -204,13 +330,15 @@ def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400, mesh=None, mats=None):
     oracle = None
     if mesh is not None:
         # the FP64 oracle band on one band of the same workload, two updates
+        from oracle import fem
         from oracle import neb as oneb
-        ops = oracle_ops(mesh, mats)
+        ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
         t = time.perf_counter()
         oneb.island_band(ops, isl.subset(np.arange(1)), p, hm, oneb.great_circle_path(ops.n, P)[None], 2, step, 1.0)
         to = time.perf_counter() - t
-        oracle = {"value": P * 2 / to, "unit": "band-image updates/s", "kind": "oracle",
-                  "cores": len(os.sched_getaffinity(0)), "sample": f"1 band x {P} images x 2 updates, {to:.1f} s"}
+        oracle = {"value": P * 2 / to, "unit": "band-image updates/s", "kind": "oracle", "cores": 1,
+                  "workers": "one process (numpy FP64; its BLAS may thread the matrix products)",
+                  "sample": f"1 band x {P} images x 2 updates, {to:.1f} s"}
     return {"image_updates_per_s": D * P * out["iters"] / wall, "unit": "band-image updates/s", "bands": D,
             "cpu_baseline": oracle,
             "images": P, "iters": out["iters"], "wall_s": wall, "max_force": out["max_force"],
@@ -251,7 +379,7 @@ def measure_ego(ctx, n=240, d=12, T=256, N=1 << 20):
     return {"nll_evals_per_s": T / t_nll, "ei_candidates_per_s": N / t_ei, "train_designs": n, "params": d,
             "theta_batch": T, "candidates": N, "note": "FP64; wall-clock per library call incl. host<->device copies",
             "cpu_baseline": {"nll_evals_per_s": o_nll, "ei_candidates_per_s": o_ei, "kind": "oracle",
-                             "cores": len(os.sched_getaffinity(0)),
+                             "cores": 1, "workers": "one process (numpy FP64; its BLAS may thread the products)",
                              "sample": "16 likelihood evaluations; EI at 16384 candidates (numpy FP64)"}}
 
 
@@ -346,33 +474,36 @@ def main_reference(args):
     if rank != 0:
         return 0
     from paper_1603_09493_gb300 import synth
-    from oracle import fem, llg
     mesh, mats, hm, p = workload()
-    isl = synth.jittered_islands(8, seed=1)
-    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
-    pp = type(p)(**{**p.__dict__})
-    # the step count of the whole workload (the field bound over all its islands), as the GPU arm uses
-    k = llg.stable_substeps(llg.Batch(ops, synth.jittered_islands(B_ISLANDS, seed=1), pp, head_map=hm))
-    bt = llg.Batch(ops, isl, pp, head_map=hm)
-    pp.substeps = k
-    pp.t_end_ps = DT_PS
-    for _ in range(args.warmup):
-        bt.run()
-    t = time.perf_counter()
-    m = None
-    for s in range(args.steps):
-        pp.t0_ps = s * DT_PS
-        pp.t_end_ps = (s + 1) * DT_PS
-        r = bt.run(m)
-        m = r["m"]
-    el = time.perf_counter() - t
-    value = len(isl) * args.steps * DT_PS * 1e-3 / el
+    k = oracle_step_count(p)        # the step count of the whole workload, as the GPU arm uses
+    W = host_cores()
+    isl = synth.jittered_islands(W, seed=1)
+    pool = OraclePool(W)
+    m = [None] * W
+
+    def step(s_):
+        q = type(p)(**{**p.__dict__})
+        q.substeps, q.t0_ps, q.t_end_ps = k, s_ * DT_PS, (s_ + 1) * DT_PS
+        return pool.run([(isl.subset([w]), q, m[w]) for w in range(W)])
+
+    try:
+        for w_ in range(args.warmup):
+            step(0)
+        t = time.perf_counter()
+        for s_ in range(args.steps):
+            m = step(s_)
+        el = time.perf_counter() - t
+    finally:
+        pool.close()
+    value = W * args.steps * DT_PS * 1e-3 / el
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(mesh, k, "fp64 (oracle)", len(isl), 1), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                             "sample": f"{len(isl)} islands per step, one 0.1 ps interval ({k} Heun steps) each"},
+            "config": config_dict(mesh, k, "fp64 (oracle)", W, 1), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": W, "kind": "oracle",
+                             "workers": f"{W} processes, one per host core, 1 BLAS thread each",
+                             "sample": f"{W} islands per step (one per worker), one 0.1 ps interval ({k} Heun "
+                                       "steps) each, the state carried from step to step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -596,8 +727,12 @@ def main(args):
                "note": "one bpm_run_batch call per run of K intervals: batch setup, graph capture, island-table "
                        "H2D, K intervals, m_final/flags D2H"}
     extras = {}
+    if rank == 0:
+        extras["parity"] = measure_parity(ctx, hid)
     if not args.no_extras and rank == 0:
         extras["plain"] = measure_plain(ctx, isl, p, hid, prec, n)
+        extras["plain_fp64"] = measure_plain_f64(ctx, isl, p, hid, mesh, mats)
+        extras["uneven"] = measure_uneven(ctx, hm, hid)
         extras["surrogate"] = measure_surrogate(ctx, torch, stream)
         extras["neb"] = measure_neb(ctx, mid, hm, hid, mesh=None if args.no_cpu else mesh,
                                     mats=None if args.no_cpu else mats)
@@ -613,7 +748,7 @@ def main(args):
             "e2e": e2e, "gpu_launches": args.steps * launches_per_interval, "roofline": roof, "roofline_step_kernels": roof_steps,
             "kernel_ms": kt, "tuning": tuning, "clocks": clocks, "status_ok": ok, **extras}
     if world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(mesh, mats, hm, p, k)
+        line["cpu_baseline"] = cpu_baseline(p, k)
     print(json.dumps(line))
     return 0
 

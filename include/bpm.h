@@ -292,6 +292,15 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t);
  * launches of the batch then return at once, and bpm_batch_read reports
  * BPM_ERR_TIMEOUT.  code = 0 clears the flag. */
 int bpm_debug_set_gemm_error(bpm_batch* bt, int32_t code);
+/* Testing aid for the failure path: the time limit (ns) of the tensor-core
+ * demag GEMM's waits for normal progress (copies landed, stages freed,
+ * accumulators full or read back); 0 restores the default of 200 ms.  A limit
+ * shorter than one output tile's MMAs (tens of microseconds) makes a real wait
+ * run out: the kernel raises the batch's error flag, lets its own copies and
+ * MMAs land (those waits keep the default limit), frees TMEM and returns, and
+ * bpm_batch_read reports BPM_ERR_TIMEOUT.  Clear the flag with
+ * bpm_debug_set_gemm_error(bt, 0) after restoring the limit. */
+int bpm_debug_set_gemm_wait(bpm_batch* bt, double wait_ns);
 /* Number of kernel launches in the batch's one-interval CUDA graph (the
  * graph exists after the first bpm_batch_advance; BPM_ERR_STATE before). */
 int bpm_batch_graph_kernels(bpm_batch* bt, int32_t* n_kernels);

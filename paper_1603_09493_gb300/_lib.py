@@ -100,6 +100,7 @@ PROTOTYPES = {
     "bpm_batch_autotune": (c_int, [c_void_p, c_int32, POINTER(bpm_tuning)]),
     "bpm_batch_set_tuning": (c_int, [c_void_p, POINTER(bpm_tuning)]),
     "bpm_debug_set_gemm_error": (c_int, [c_void_p, c_int32]),
+    "bpm_debug_set_gemm_wait": (c_int, [c_void_p, c_double]),
     "bpm_batch_graph_kernels": (c_int, [c_void_p, POINTER(c_int32)]),
     "bpm_neb_run": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_neb_params), c_void_p, c_int32, c_void_p,
                             c_void_p, c_void_p, POINTER(c_int32), POINTER(c_double)]),

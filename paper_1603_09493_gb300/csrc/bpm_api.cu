@@ -1173,6 +1173,18 @@ int bpm_debug_set_gemm_error(bpm_batch* bt, int32_t code) {
     return BPM_OK;
 }
 
+int bpm_debug_set_gemm_wait(bpm_batch* bt, double wait_ns) {
+    if (!bt || !(wait_ns >= 0) || wait_ns > 1e10) {
+        set_error("bad wait limit (0 for the default, else up to 1e10 ns)");
+        return BPM_ERR_ARG;
+    }
+    BPM_TRY(ensure_device(bt->ctx));
+    BPM_CK(cudaStreamSynchronize(bt->ctx->stream));
+    bt->gg.wait_ns = (unsigned long long)wait_ns;
+    drop_graph(bt);   // the graph holds the old kernel arguments
+    return BPM_OK;
+}
+
 int bpm_batch_time(bpm_batch* bt, double* t_ps) {
     if (!bt || !t_ps) {
         set_error("null argument");

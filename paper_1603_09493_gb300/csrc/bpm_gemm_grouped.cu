@@ -16,6 +16,9 @@
 // Per-group tensor maps live in a device array (64-byte aligned entries).
 // Every wait is bounded; on timeout the kernel raises the error flag, drains
 // its copies and MMAs, frees TMEM and exits, and later launches return at once.
+// The waits of normal progress take the launch's limit (wait_ns); the drains
+// always take the fixed limit, so that copies and MMAs land before shared
+// memory or TMEM is given up.
 #include <cstring>
 
 #include "bpm_tc_ptx.cuh"
@@ -61,7 +64,7 @@ __device__ __forceinline__ void tile_origin(const GemmGroupDev& gg, int lt, int&
 
 template <int P, int TN, int KB>
 __global__ void __launch_bounds__(kGThreads, 1)
-    k_gemm_grouped(const GemmGroupDev* __restrict__ G, int ng, int total_tiles, int* err) {
+    k_gemm_grouped(const GemmGroupDev* __restrict__ G, int ng, int total_tiles, int* err, unsigned long long wait_ns) {
     using CF = GCfg<P, TN, KB>;
     constexpr int S = CF::stages;
     constexpr int A_TILE = CF::A_BYTES;
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             const int nk = gg.K / KB;
             for (int kb = 0; kb < nk; ++kb, ++kbg) {
                 const int s = kbg % S;
-                if (kbg >= S) ok = mbar_wait(empty_bar(s), ((kbg / S) - 1) & 1, err, 11);
+                if (kbg >= S) ok = mbar_wait(empty_bar(s), ((kbg / S) - 1) & 1, err, 11, true, wait_ns);
                 if (!ok) break;
                 mbar_expect_tx(full_bar(s), CF::stage_bytes);
                 const int kc = kb * KB;
@@ -152,13 +155,13 @@ __global__ void __launch_bounds__(kGThreads, 1)
             // a ragged last column tile runs MMAs only as wide as its valid columns (N % 16 == 0)
             const uint32_t idesc = idesc_n<TN>(min(TN, gg.N - n0));
             const int a = i & 1;
-            if (i >= 2) ok = mbar_wait(acce_bar(a), ((i >> 1) - 1) & 1, err, 13);
+            if (i >= 2) ok = mbar_wait(acce_bar(a), ((i >> 1) - 1) & 1, err, 13, true, wait_ns);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc = tmem + (uint32_t)(a * TN);
             for (int kb = 0; kb < nk; ++kb, ++kbg) {
                 const int s = kbg % S;
-                ok = mbar_wait(full_bar(s), (kbg / S) & 1, err, 14);
+                ok = mbar_wait(full_bar(s), (kbg / S) & 1, err, 14, true, wait_ns);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             int m0, n0;
             tile_origin<TN>(gg, t - gg.tile_begin, m0, n0);
             const int a = i & 1;
-            const bool have = mbar_wait(accf_bar(a), (i >> 1) & 1, err, 15);
+            const bool have = mbar_wait(accf_bar(a), (i >> 1) & 1, err, 15, true, wait_ns);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int go = __shfl_sync(0xffffffffu, (have && *(volatile int*)err == 0) ? 1 : 0, 0);
             if (!go) break;
@@ -233,7 +236,8 @@ int launch_grouped(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err
     }
     const int grid = std::max(1, std::min(gg.total_tiles, sm_count));
     k_gemm_grouped<P, TN, KB>
-        <<<grid, kGThreads, GCfg<P, TN, KB>::smem, s>>>(gg.d_groups, gg.n_groups, gg.total_tiles, err);
+        <<<grid, kGThreads, GCfg<P, TN, KB>::smem, s>>>(gg.d_groups, gg.n_groups, gg.total_tiles, err,
+                                                        gg.wait_ns ? gg.wait_ns : kWaitNs);
     BPM_CK(cudaGetLastError());
     return BPM_OK;
 }

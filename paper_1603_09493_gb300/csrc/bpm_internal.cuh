@@ -169,6 +169,7 @@ struct GemmOperands {
 struct GroupedGemm {
     GemmGroupDev* d_groups = nullptr;
     int n_groups = 0, total_tiles = 0, tile_n = 256, products = 3, k_block = 64;
+    unsigned long long wait_ns = 0;   // limit of the non-drain waits (0: the default)
 };
 // k_block: K depth of one pipeline stage, 64 (128-byte swizzle) or 32 (64-byte swizzle, twice the stages)
 int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products, int raster,

@@ -47,6 +47,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// non-blocking test of a phase (try_wait may suspend the thread until the phase completes)
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -58,13 +73,27 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // flag.  Waits that guard the lifetime of shared memory or TMEM (copies or MMAs still in
 // flight) pass heed_err = false, so that they end only when the work has landed or the
 // time limit has passed.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, bool heed_err = true) {
+// limit_ns bounds the waits of a kernel's normal progress (kWaitNs unless a caller shortens it
+// to exercise the failure path); drains always take kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, bool heed_err = true,
+                                          unsigned long long limit_ns = kWaitNs) {
+    if (limit_ns < kWaitNs) {
+        // a shortened limit: non-blocking polls with the clock read after each, so that a
+        // limit below the time the phase takes is sure to run out
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+            if (mbar_test_wait(bar, parity)) return true;
+            if (global_ns() - t0 > limit_ns || (heed_err && *(volatile int*)err != 0)) break;
+        }
+        atomicExch(err, code);
+        return false;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 256; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs || (heed_err && *(volatile int*)err != 0)) break;
+        if (global_ns() - t0 > limit_ns || (heed_err && *(volatile int*)err != 0)) break;
     }
     atomicExch(err, code);
     return false;
@@ -72,7 +101,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
 
 // wait for work in flight (copies, MMAs) before shared memory or TMEM is given up
 __device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, int* err, int code) {
-    return mbar_wait(bar, parity, err, code, false);
+    return mbar_wait(bar, parity, err, code, false, kWaitNs);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {

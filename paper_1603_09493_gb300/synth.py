@@ -332,6 +332,32 @@ def uniform_field(B_T: float, angle_deg: float) -> tuple:
     return (B_T * math.sin(a), 0.0, B_T * math.cos(a))
 
 
+def census_run_params(t_end_ps: float = 0.1) -> RunParams:
+    """The census workload's run: head map moving at 20 m/s from 10 nm before the
+    island, 100 ps field rise, damping 0.1, 0.1 ps output intervals."""
+    return RunParams(dt_ps=0.1, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=-10.0, use_map=True,
+                     t_end_ps=t_end_ps)
+
+
+def head_field_direction(tilt_deg: float = 25.0) -> np.ndarray:
+    """Unit direction of the synthetic head field, (0, sin tilt, -cos tilt)."""
+    th = math.radians(tilt_deg)
+    return np.array([0.0, math.sin(th), -math.cos(th)])
+
+
+def outcome_census(B: int = 1024, seed: int = 5, mesh_id: int = 0, H_max_T: float = 0.3):
+    """A recording census of Sec. II.C shape: B jittered islands written by the head
+    moving at 20 m/s from 2 nm before them (100 ps rise, damping 0.1, 300 ps),
+    island b under a constant field of (b / B) H_max_T opposing the head field, so
+    that the outcomes range from nearly all switched to nearly none.  Returns
+    (Islands, RunParams)."""
+    isl = jittered_islands(B, seed=seed, mesh_id=mesh_id)
+    mag = H_max_T * np.arange(B) / B
+    isl.Hext_T[:] = (-mag[:, None] * head_field_direction()[None, :]).astype(np.float32)
+    p = RunParams(dt_ps=0.1, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=-2.0, use_map=True, t_end_ps=300.0)
+    return isl, p
+
+
 def small_island_mesh(seed: int = 0) -> IslandMesh:
     """~200-node island: 19-node disk x 11 planes (hard 7 x 1 nm, soft 3 x 1 nm)."""
     return layered_island_mesh(8.0, 7.0, 3.0, rings=2, hard_slabs=7, soft_slabs=3, seed=seed)

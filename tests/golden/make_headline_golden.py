@@ -14,17 +14,17 @@ for these runs, more than a test may take, so its results are stored:
               of at most 1.6e-5).
   outcomes    tests/golden/outcome_census_209.npz
               1024 jittered islands of the 209-node mesh written by the moving
-              head (Sec. II.C recording simulation: the head field plus a
-              constant field H_ext opposing it, spread over the islands so that
-              a real fraction of them switches); the switch flag, first
-              crossing time and final volume-averaged m_z of every island.
+              head (synth.outcome_census, a Sec. II.C recording simulation: the
+              head field plus a constant field H_ext opposing it, spread over
+              the islands so that a real fraction of them switches), 300 ps;
+              the switch flag, first crossing time and final volume-averaged
+              m_z of every island.
 
   python tests/golden/make_headline_golden.py census|outcomes [--workers N]
 """
 from __future__ import annotations
 
 import argparse
-import math
 import multiprocessing as mp
 import os
 import sys
@@ -43,44 +43,24 @@ CENSUS_SAMPLES = 64
 CENSUS_INTERVALS = 1000          # 100 ps at 0.1 ps
 CENSUS_SNAPSHOT_EVERY = 100      # full state every 10 ps
 
-# outcome census
-OUTCOME_B = 1024
-OUTCOME_SEED = 5
-OUTCOME_T_END_PS = 500.0
-OUTCOME_X0_NM = -4.0
-OUTCOME_HEXT_MAX_T = 0.3
-
 
 def census_params():
     from paper_1603_09493_gb300 import synth
-    return synth.RunParams(dt_ps=0.1, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=-10.0, use_map=True,
-                           t_end_ps=CENSUS_INTERVALS * 0.1)
+    return synth.census_run_params(t_end_ps=CENSUS_INTERVALS * 0.1)
 
 
 def census_sample_index() -> np.ndarray:
     return np.round(np.linspace(0, CENSUS_B - 1, CENSUS_SAMPLES)).astype(np.int64)
 
 
-def head_direction() -> np.ndarray:
-    """Unit direction of the synthetic head field (under the pole): (0, sin 25, -cos 25)."""
-    th = math.radians(25.0)
-    return np.array([0.0, math.sin(th), -math.cos(th)])
-
-
 def outcome_islands(mesh_id: int = 0):
-    """1024 jittered islands; island b carries H_ext = -(b / B) * 0.3 T along the head
-    field direction (the Sec. II.C field that opposes writing the target bit)."""
     from paper_1603_09493_gb300 import synth
-    isl = synth.jittered_islands(OUTCOME_B, seed=OUTCOME_SEED, mesh_id=mesh_id)
-    mag = OUTCOME_HEXT_MAX_T * np.arange(OUTCOME_B) / OUTCOME_B
-    isl.Hext_T[:] = (-mag[:, None] * head_direction()[None, :]).astype(np.float32)
-    return isl
+    return synth.outcome_census(mesh_id=mesh_id)[0]
 
 
 def outcome_params():
     from paper_1603_09493_gb300 import synth
-    return synth.RunParams(dt_ps=0.1, alpha=0.1, rise_ps=100.0, v_m_per_s=20.0, x0_nm=OUTCOME_X0_NM, use_map=True,
-                           t_end_ps=OUTCOME_T_END_PS)
+    return synth.outcome_census()[1]
 
 
 def _census_chunk(args):
@@ -158,7 +138,7 @@ def make_outcomes(workers: int):
     p = outcome_params()
     isl = outcome_islands()
     k = llg.stable_substeps(llg.Batch(ops, isl, p, head_map=synth.synthetic_head_map(), demag=np.zeros((1, 1))))
-    bounds = np.linspace(0, OUTCOME_B, 4 * workers + 1).astype(int)
+    bounds = np.linspace(0, len(isl), 4 * workers + 1).astype(int)
     t = time.time()
     with _pool(workers) as pool:
         res = pool.map(_outcome_chunk, [(bounds[i], bounds[i + 1], k) for i in range(len(bounds) - 1)])
@@ -169,7 +149,7 @@ def make_outcomes(workers: int):
     out = os.path.join(GOLDEN, "outcome_census_209.npz")
     np.savez_compressed(out, k=k, switched=sw, t_sw=tsw, mz=mz, status=st, Ms_scale=isl.Ms_scale,
                         Ku_scale=isl.Ku_scale, u=isl.u, pos_nm=isl.pos_nm, Hext_T=isl.Hext_T,
-                        t_end_ps=OUTCOME_T_END_PS)
+                        t_end_ps=outcome_params().t_end_ps)
     print(f"outcomes: k={k}, {sw.sum()} of {sw.size} switched, {time.time() - t:.0f} s -> {out}")
 
 

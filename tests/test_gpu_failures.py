@@ -86,3 +86,30 @@ def test_gemm_error_flag_reports_timeout_and_clears(ctx, mid):
         bt.advance(2)
         out = bt.read()
         assert np.all(out["status"] == 0)
+
+
+def test_a_real_gemm_wait_runs_out_and_the_batch_recovers(ctx, mid):
+    # a wait limit far below one output tile's MMAs: the first tile's accumulator is not full
+    # in time, the wait gives up, the kernel lets its copies and MMAs land, frees TMEM and
+    # returns; the batch reports BPM_ERR_TIMEOUT, and after the limit is restored and the
+    # flag cleared the same run gives the same state as a batch that never timed out
+    isl = synth.jittered_islands(300, seed=5, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, substeps=4, alpha=0.1, rise_ps=10.0, uniform_T=(0.0, 0.0, -0.6))
+    with ctx.batch(isl, p, precision=L.PREC_BF16X3) as bt:
+        bt.advance(3)
+        clean = bt.read()
+    with ctx.batch(isl, p, precision=L.PREC_BF16X3) as bt:
+        L.check(ctx.lib.bpm_debug_set_gemm_wait(bt.h, 1000.0))        # 1 us
+        bt.advance(3)
+        with pytest.raises(L.BpmError) as e:
+            bt.read()
+        assert e.value.code == L.BPM_ERR_TIMEOUT
+        L.check(ctx.lib.bpm_debug_set_gemm_wait(bt.h, 0.0))
+        L.check(ctx.lib.bpm_debug_set_gemm_error(bt.h, 0))
+        bt.set_state(None, 0.0)
+        bt.advance(3)
+        out = bt.read()
+    assert np.array_equal(out["m"], clean["m"])
+    assert np.all(out["status"] == 0)
+    with pytest.raises(L.BpmError):
+        L.check(ctx.lib.bpm_debug_set_gemm_wait(None, 5.0))
