@@ -130,9 +130,8 @@ def gemm_traffic(prec, B, n):
 
 
 # ---------------------------------------------------------------------------
-# The FP64 oracle on the host cores: one spawned worker process per core, each
-# with one BLAS thread and its own copy of the census mesh operators, each
-# integrating its own islands.
+# The FP64 oracle on the host cores: spawned worker processes, each with its
+# own copy of the census mesh operators and a pinned number of BLAS threads.
 
 _WORKER = {}
 
@@ -153,14 +152,15 @@ def _oracle_worker_run(task):
 
 
 class OraclePool:
-    """Worker processes with the census workload's oracle operators built; the
-    constructor returns once every worker holds them, so that timing starts
-    after the set-up."""
+    """Worker processes with the census workload's oracle operators built, each
+    with `threads` BLAS threads (pinned through the environment before numpy
+    loads); the constructor returns once every worker holds them, so that
+    timing starts after the set-up."""
 
-    def __init__(self, workers: int):
+    def __init__(self, workers: int, threads: int = 1):
         import multiprocessing as mp
         for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-            os.environ[v] = "1"
+            os.environ[v] = str(int(threads))
         ctx = mp.get_context("spawn")
         barrier = ctx.Barrier(workers + 1)
         self.workers = workers
@@ -190,18 +190,19 @@ def oracle_step_count(p):
 
 
 def cpu_baseline(p, k, target_s=15.0):
-    """The oracle on all host cores: one island per worker, a bounded number of
-    0.1 ps intervals sized to about target_s seconds."""
+    """The oracle on all host cores: one process integrating one island per core
+    as one batch, its BLAS pinned to as many threads as the host has cores, for
+    a bounded number of 0.1 ps intervals sized to about target_s seconds."""
     from paper_1603_09493_gb300 import synth
     W = host_cores()
     isl = synth.jittered_islands(W, seed=1)
-    pool = OraclePool(W)
+    pool = OraclePool(1, threads=W)
     try:
         def run(nint):
             q = type(p)(**{**p.__dict__})
             q.substeps, q.t0_ps, q.t_end_ps = k, 0.0, nint * DT_PS
             t = time.perf_counter()
-            pool.run([(isl.subset([w]), q, None) for w in range(W)])
+            pool.run([(isl, q, None)])
             return time.perf_counter() - t
         t1 = run(1)
         nint = int(max(1, min(40, round(target_s / max(t1, 1e-3)))))
@@ -209,9 +210,14 @@ def cpu_baseline(p, k, target_s=15.0):
     finally:
         pool.close()
     return {"value": W * nint * DT_PS * 1e-3 / t, "unit": UNIT, "cores": W, "kind": "oracle",
-            "workers": f"{W} processes, one per host core, 1 BLAS thread each",
-            "sample": f"{W} islands (one per worker) x {nint} intervals ({nint * k} Heun steps) of the census "
+            "workers": f"one process, its BLAS pinned to {W} threads (one per host core)",
+            "sample": f"{W} islands in one oracle batch x {nint} intervals ({nint * k} Heun steps) of the census "
                       f"workload, numpy FP64, {t:.1f} s"}
+
+
+def stable_k(ctx, hid, isl, p):
+    """The library's integrator step count for this workload (bpm_stable_substeps)."""
+    return ctx.stable_substeps(isl, p, hid)[0]
 
 
 def measure_plain(ctx, isl, p, hid, prec, n, islands=8, intervals=2):
@@ -430,43 +436,81 @@ def measure_surrogate(ctx, torch, stream, n_infer=262144, n_train=65536, batch=4
                     "wall-clock per call including the host->device copy of the data"}
 
 
-def measure_search(ctx, generations=20, population=256, top_k=32, n_jit_screen=64, n_jit_verify=128,
-                   n_train=4096):
-    """Surrogate-assisted design search on the 209-node mesh: the surrogate is
-    trained on LLG outcomes of random designs, screens every generation, and
-    only the best-screened designs are solved with LLG.  Wall-clock of each
-    part, against solving every design of every generation with LLG at the
-    loop's own LLG rate."""
-    import numpy as np
-    from paper_1603_09493_gb300 import evolve, synth
-    mesh = synth.small_island_mesh()
-    mid = ctx.mesh_upload(mesh, synth.ecc_materials())
-    p = evolve.run_params(100.0)
+def measure_search(ctx, generations=8, population=256, top_k=16, n_jit_screen=64, n_jit_verify=64,
+                   n_train=32768, n_heads=128, n_heldout=4096):
+    """The surrogate on the write-head and media design problem (design.py: 12
+    design and 4 jitter inputs, labels from LLG batches over the 81-mesh
+    geometry grid with the moving head map and the layout's adjacent-track
+    island): LLG labels of random designs, training, held-out error against
+    fresh LLG solves of unseen designs and heads, then the surrogate-assisted
+    design search.  Wall-clock of each part; the LLG-only time is every design
+    of every generation solved at the loop's own LLG rate."""
+    from paper_1603_09493_gb300 import design, evolve, synth
+    grid = design.upload_grid(ctx)
     t0 = time.perf_counter()
-    Zt = synth.counter_uniform(41, 0, np.arange(n_train * 4)).reshape(n_train, 4)
-    tgt, adj, Xt = evolve.samples(Zt, 1, seed=42, first_index=0, mesh_id=mid)
-    Yt = evolve.llg_outcomes(ctx, mid, p, tgt, adj)
+    X, Y, _ = design.training_set(ctx, grid, n_train, n_heads, seed=41)
     label_s = time.perf_counter() - t0
+    Xh, Yh, _ = design.training_set(ctx, grid, n_heldout, 16, seed=42, first_index=10 ** 6)
     sur = ctx.surrogate((16, 256, 4, 2), synth.mlp_init_params([16, 256, 256, 256, 256, 2], seed=4))
     t0 = time.perf_counter()
-    sur.train(Xt, Yt, epochs=60, batch=512, lr=2e-3, weight_decay=1e-4)
+    sur.train(X, Y, epochs=40, batch=512, lr=2e-3, weight_decay=1e-4)
     train_s = time.perf_counter() - t0
+    P = sur.infer(Xh)
+    held = {"target": design.metrics(P[:, 0], Yh[:, 0]), "adjacent": design.metrics(P[:, 1], Yh[:, 1])}
     cfg = evolve.SearchConfig(generations=generations, population=population, top_k=top_k,
                               n_jitter_screen=n_jit_screen, n_jitter_verify=n_jit_verify, seed=43)
-    res = evolve.search(ctx, sur, mid, cfg, t_end_ps=100.0)
+    res = design.search(ctx, sur, grid, cfg)
     sur.destroy()
-    best = evolve.design_values(res.best_Z[None])
+    best = design.values(res.best_Z[None])
     loop_s = res.screen_s + res.verify_s
-    return {"generations": generations, "population": population, "top_k": top_k,
-            "n_jitter_screen": n_jit_screen, "n_jitter_verify": n_jit_verify, "mesh_nodes": int(mesh.n_nodes),
-            "t_end_ps": 100.0, "best_design": {k: float(v[0]) for k, v in best.items()},
-            "best_write_ber": float(res.best_rates[0]), "best_adjacent_rate": float(res.best_rates[1]),
+    return {"problem": "12 design parameters (diameter, t_soft, t_hard, Ms, Ku, interlayer exchange, pitch, "
+                       "layout, head peak, tilt, width, velocity) + 4 jitter values; labels: target switched, "
+                       "adjacent-track island flipped; 81-mesh geometry grid, moving head map, 250 ps",
+            "train_labels": n_train, "label_islands": 2 * n_train, "heads": n_heads, "heldout_labels": n_heldout,
+            "heldout": held, "generations": generations, "population": population, "top_k": top_k,
+            "n_jitter_screen": n_jit_screen, "n_jitter_verify": n_jit_verify,
+            "best_design": {k: float(v[0]) for k, v in best.items()},
+            "best_write_error_rate": float(res.best_rates[0]), "best_adjacent_flip_rate": float(res.best_rates[1]),
             "best_per_generation": [h["best_verified"] for h in res.history],
             "train_labels_s": label_s, "train_s": train_s, "screen_s": res.screen_s, "verify_s": res.verify_s,
             "llg_only_s": res.llg_only_s, "loop_vs_llg_only": res.llg_only_s / loop_s,
-            "note": f"{n_jit_verify} LLG jitter samples per verified design (not 4096); LLG-only time is every "
-                    "design of every generation solved at the loop's measured LLG rate; wall-clock incl. host "
-                    "copies; an error rate of 0 means none of the verified samples failed"}
+            "note": f"{n_jit_verify} LLG jitter samples per verified design (not 4096); an error rate of 0 means "
+                    "none of the verified samples failed; wall-clock incl. host copies and head-map uploads"}
+
+
+def main_surrogate_study(args):
+    """The surrogate's label-count study on the design problem: LLG labels of
+    random designs in rounds, training on the growing set, held-out error
+    against fresh LLG solves after each round; one JSON line."""
+    import torch
+    from paper_1603_09493_gb300 import api, design, synth
+    torch.cuda.set_device(0)
+    ctx = api.Context(0, stream=torch.cuda.Stream())
+    grid = design.upload_grid(ctx)
+    Xh, Yh, _ = design.training_set(ctx, grid, 8192, 16, seed=52, first_index=10 ** 7)
+    Xs, Ys, rows = [], [], []
+    t_label = 0.0
+    per_round = args.study_round
+    for r in range(args.study_rounds):
+        t0 = time.perf_counter()
+        X, Y, _ = design.training_set(ctx, grid, per_round, 128, seed=51, first_index=r * per_round)
+        t_label += time.perf_counter() - t0
+        Xs.append(X)
+        Ys.append(Y)
+        Xa, Ya = np.concatenate(Xs), np.concatenate(Ys)
+        sur = ctx.surrogate((16, 256, 4, 2), synth.mlp_init_params([16, 256, 256, 256, 256, 2], seed=4))
+        t0 = time.perf_counter()
+        sur.train(Xa, Ya, epochs=max(10, int(40 * 32768 / len(Xa))), batch=1024, lr=2e-3, weight_decay=1e-4)
+        t_train = time.perf_counter() - t0
+        P = sur.infer(Xh)
+        sur.destroy()
+        rows.append({"labels": len(Xa), "target": design.metrics(P[:, 0], Yh[:, 0]),
+                     "adjacent": design.metrics(P[:, 1], Yh[:, 1]), "label_s_total": t_label, "train_s": t_train})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    ctx.close()
+    print(json.dumps({"workload": "surrogate label-count study on the design problem", "heldout_labels": 8192,
+                      "rounds": rows}))
+    return 0
 
 
 def main_reference(args):
@@ -478,13 +522,13 @@ def main_reference(args):
     k = oracle_step_count(p)        # the step count of the whole workload, as the GPU arm uses
     W = host_cores()
     isl = synth.jittered_islands(W, seed=1)
-    pool = OraclePool(W)
-    m = [None] * W
+    pool = OraclePool(1, threads=W)
+    m = None
 
     def step(s_):
         q = type(p)(**{**p.__dict__})
         q.substeps, q.t0_ps, q.t_end_ps = k, s_ * DT_PS, (s_ + 1) * DT_PS
-        return pool.run([(isl.subset([w]), q, m[w]) for w in range(W)])
+        return pool.run([(isl, q, m)])[0]
 
     try:
         for w_ in range(args.warmup):
@@ -501,8 +545,8 @@ def main_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(mesh, k, "fp64 (oracle)", W, 1), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": W, "kind": "oracle",
-                             "workers": f"{W} processes, one per host core, 1 BLAS thread each",
-                             "sample": f"{W} islands per step (one per worker), one 0.1 ps interval ({k} Heun "
+                             "workers": f"one process, its BLAS pinned to {W} threads (one per host core)",
+                             "sample": f"{W} islands per step in one oracle batch, one 0.1 ps interval ({k} Heun "
                                        "steps) each, the state carried from step to step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -613,6 +657,8 @@ def main(args):
         return main_uneven(args)
     if args.workload == "extras":
         return main_extras(args)
+    if args.workload == "surrogate-study":
+        return main_surrogate_study(args)
     import torch
     from paper_1603_09493_gb300 import _lib as L
     from paper_1603_09493_gb300 import api, synth
@@ -765,7 +811,10 @@ if __name__ == "__main__":
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", default="census", choices=["census", "uneven", "extras", "surrogate"])
+    ap.add_argument("--workload", default="census",
+                    choices=["census", "uneven", "extras", "surrogate", "surrogate-study"])
+    ap.add_argument("--study-round", type=int, default=32768, help="labels per round of the surrogate study")
+    ap.add_argument("--study-rounds", type=int, default=4)
     ap.add_argument("--realisations", type=int, default=512)
     ap.add_argument("--clock-log", default="", help="also write the raw nvidia-smi clock samples here")
     sys.exit(main(ap.parse_args()))

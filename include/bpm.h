@@ -264,20 +264,23 @@ int bpm_batch_kernel_times(bpm_batch* bt, int32_t reps, double* gemm_ms, double*
 enum { BPM_RASTER_AUTO = 0, BPM_RASTER_M = 1, BPM_RASTER_N = 2 };
 
 /* Launch configuration of a batch's kernels.  A new batch starts with
- * gemm_tile_n 256, stage_threads 256, gemm_raster AUTO, stage_islands 2 and
- * gemm_k_block 32 (the fastest on the census and uneven batches measured). */
+ * gemm_tile_n 256, stage_threads 256, gemm_raster AUTO, stage_islands 2,
+ * gemm_k_block 32 and gemm_pair 0 (the fastest on the census and uneven
+ * batches measured). */
 typedef struct {
     int32_t gemm_tile_n;     /* output columns per demag-GEMM CTA: 256 or 128 */
     int32_t stage_threads;   /* threads per Heun-stage CTA: 128, 256 or 512 */
     int32_t gemm_raster;     /* BPM_RASTER_*: tile order of the tensor-core GEMM */
     int32_t stage_islands;   /* islands per Heun-stage CTA: 1 (0 = 1), or 2 with 256 threads */
     int32_t gemm_k_block;    /* K depth of a tensor-core GEMM pipeline stage: 32 (0 = 32) or 64 */
-    int32_t reserved;        /* 0 */
+    int32_t gemm_pair;       /* 1: 256 x 256 GEMM tiles on the two SMs of a CTA pair (tcgen05
+                                cta_group::2; needs gemm_tile_n 256), 0: 128 x gemm_tile_n tiles
+                                on one SM */
     double  gemm_ms;         /* measured time of one demag GEMM over the batch (autotune output) */
     double  stage_ms;        /* measured time of one predictor + one corrector over the batch */
 } bpm_tuning;
 
-/* Autotuner: time every (gemm_tile_n, gemm_raster, gemm_k_block) candidate of the demag GEMM
+/* Autotuner: time every (gemm_tile_n, gemm_raster, gemm_k_block, gemm_pair) candidate of the demag GEMM
  * and every (stage_threads, stage_islands) candidate on this batch with CUDA events (reps Heun
  * steps each, kernel by kernel), apply the fastest of each, and report them in
  * *chosen (nullable).  The

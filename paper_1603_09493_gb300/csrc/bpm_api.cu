@@ -137,6 +137,7 @@ struct bpm_batch {
     int tile_n = 256;                 // demag GEMM output columns per CTA
     int raster = BPM_RASTER_AUTO;     // demag GEMM tile order
     int k_block = 32;                 // demag GEMM K depth per pipeline stage
+    int pair = 0;                     // demag GEMM on CTA pairs (256 x 256 tiles)
     GroupedGemm gg;                   // tensor-core demag GEMM over all groups (BF16 precisions)
 };
 
@@ -175,7 +176,7 @@ int setup_grouped_gemm(bpm_batch* bt) {
         ops.push_back(GemmOperands{g.Ahi, g.Alo, g.mesh->Nhi, g.mesh->Nlo, g.Hd, g.Bp, K, K});
     }
     return grouped_gemm_setup(&bt->gg, ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1, bt->raster,
-                              bt->k_block, bt->ctx->l2_bytes);
+                              bt->k_block, bt->ctx->l2_bytes, bt->pair);
 }
 
 // demag GEMM of every group's current operand A -> Hd: one persistent launch
@@ -1094,9 +1095,11 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
         (t->stage_threads != 128 && t->stage_threads != 256 && t->stage_threads != 512) ||
         (t->gemm_raster != BPM_RASTER_AUTO && t->gemm_raster != BPM_RASTER_M && t->gemm_raster != BPM_RASTER_N) ||
         t->stage_islands < 0 || t->stage_islands > 2 || (t->stage_islands == 2 && t->stage_threads != 256) ||
-        (t->gemm_k_block != 0 && t->gemm_k_block != 32 && t->gemm_k_block != 64)) {
+        (t->gemm_k_block != 0 && t->gemm_k_block != 32 && t->gemm_k_block != 64) || t->gemm_pair < 0 ||
+        t->gemm_pair > 1 || (t->gemm_pair == 1 && t->gemm_tile_n != 256)) {
         set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512, gemm_raster 0|1|2, "
-                  "stage_islands 0|1|2 with 2 only at 256 threads, gemm_k_block 0|32|64)");
+                  "stage_islands 0|1|2 with 2 only at 256 threads, gemm_k_block 0|32|64, gemm_pair 0|1 with 1 "
+                  "only at gemm_tile_n 256)");
         return BPM_ERR_ARG;
     }
     BPM_TRY(ensure_device(bt->ctx));
@@ -1104,6 +1107,7 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
     bt->tile_n = t->gemm_tile_n;
     bt->raster = t->gemm_raster;
     bt->k_block = t->gemm_k_block == 64 ? 64 : 32;
+    bt->pair = t->gemm_pair;
     for (auto& g : bt->groups) {
         g.args.threads = t->stage_threads;
         g.args.ipb = t->stage_islands == 2 ? 2 : 1;
@@ -1118,18 +1122,20 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
         set_error("bad autotune arguments");
         return BPM_ERR_ARG;
     }
-    const int tiles[2] = {256, 128};
+    // (tile width, CTA pair): one-SM tiles 256 or 128 wide, or 256 x 256 tiles on CTA pairs
+    const int tiles[3] = {256, 128, 256};
+    const int pairs[3] = {0, 0, 1};
     const int rasters[3] = {BPM_RASTER_AUTO, BPM_RASTER_M, BPM_RASTER_N};
     const int kblocks[2] = {64, 32};
     const int threads[3] = {256, 128, 512};
     const bool tc = tensor_core_precision(bt);
     double best_g = 1e300, best_s = 1e300;
-    int bt_n = 256, bt_r = BPM_RASTER_AUTO, bt_t = 256, bt_k = 64;
+    int bt_n = 256, bt_r = BPM_RASTER_AUTO, bt_t = 256, bt_k = 64, bt_p = 0;
     // the GEMM candidates at the default stage CTA size, then the stage CTA sizes at the best GEMM
-    for (int ti = 0; ti < (tc ? 2 : 1); ++ti)
+    for (int ti = 0; ti < (tc ? 3 : 1); ++ti)
         for (int ri = 0; ri < (tc ? 3 : 1); ++ri)
             for (int ki = 0; ki < (tc ? 2 : 1); ++ki) {
-                bpm_tuning t{tiles[ti], 256, rasters[ri], 1, kblocks[ki], 0, 0, 0};
+                bpm_tuning t{tiles[ti], 256, rasters[ri], 1, kblocks[ki], pairs[ti], 0, 0};
                 BPM_TRY(bpm_batch_set_tuning(bt, &t));
                 double g = 0, s1 = 0, s2 = 0;
                 BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));   // warm-up
@@ -1139,13 +1145,14 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
                     bt_n = tiles[ti];
                     bt_r = rasters[ri];
                     bt_k = kblocks[ki];
+                    bt_p = pairs[ti];
                 }
             }
     // stage candidates: one island per CTA at each CTA size, two islands per 256-thread CTA
     int bt_i = 1;
     for (int hi = 0; hi < 4; ++hi) {
         const int nt = hi < 3 ? threads[hi] : 256, ipb = hi < 3 ? 1 : 2;
-        bpm_tuning t{bt_n, nt, bt_r, ipb, bt_k, 0, 0, 0};
+        bpm_tuning t{bt_n, nt, bt_r, ipb, bt_k, bt_p, 0, 0};
         BPM_TRY(bpm_batch_set_tuning(bt, &t));
         double g = 0, s1 = 0, s2 = 0;
         BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));
@@ -1156,7 +1163,7 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
             bt_i = ipb;
         }
     }
-    bpm_tuning t{bt_n, bt_t, bt_r, bt_i, bt_k, 0, best_g, best_s};
+    bpm_tuning t{bt_n, bt_t, bt_r, bt_i, bt_k, bt_p, best_g, best_s};
     BPM_TRY(bpm_batch_set_tuning(bt, &t));
     if (chosen) *chosen = t;
     return BPM_OK;

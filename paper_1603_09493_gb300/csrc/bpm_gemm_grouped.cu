@@ -245,7 +245,11 @@ int launch_grouped(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err
 }  // namespace
 
 int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products, int raster,
-                       int k_block, size_t l2_bytes) {
+                       int k_block, size_t l2_bytes, int pair) {
+    if (pair && tile_n != 256) {
+        set_error("the CTA-pair GEMM computes 256 x 256 tiles (tile_n 256)");
+        return BPM_ERR_ARG;
+    }
     if (k_block != 64 && k_block != 32) {
         set_error("grouped GEMM k-block must be 64 or 32");
         return BPM_ERR_ARG;
@@ -268,11 +272,13 @@ int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, in
             return BPM_ERR_ARG;
         }
         std::memset(&h[g], 0, sizeof(GemmGroupDev));
+        // a CTA of a pair stages 128 of the tile's 256 W rows
+        const int w_box = pair ? tile_n / 2 : tile_n;
         BPM_TRY(make_bf16_tensor_map(&h[g].ahi, o.Ahi, o.K, o.M, tc::TM, k_block));
-        BPM_TRY(make_bf16_tensor_map(&h[g].whi, o.Whi, o.K, o.N, tile_n, k_block));
+        BPM_TRY(make_bf16_tensor_map(&h[g].whi, o.Whi, o.K, o.N, w_box, k_block));
         if (products == 3) {
             BPM_TRY(make_bf16_tensor_map(&h[g].alo, o.Alo, o.K, o.M, tc::TM, k_block));
-            BPM_TRY(make_bf16_tensor_map(&h[g].wlo, o.Wlo, o.K, o.N, tile_n, k_block));
+            BPM_TRY(make_bf16_tensor_map(&h[g].wlo, o.Wlo, o.K, o.N, w_box, k_block));
         } else {
             h[g].alo = h[g].ahi;
             h[g].wlo = h[g].whi;
@@ -282,7 +288,7 @@ int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, in
         h[g].N = o.N;
         h[g].K = o.K;
         h[g].ldc = o.N;
-        h[g].tiles_m = o.M / tc::TM;
+        h[g].tiles_m = pair ? (o.M + 2 * tc::TM - 1) / (2 * tc::TM) : o.M / tc::TM;
         h[g].tiles_n = (o.N + tile_n - 1) / tile_n;
         h[g].tile_begin = tiles;
         // AUTO: N-major when the operator has more rows than the batch operand, so that the
@@ -300,6 +306,7 @@ int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, in
     gg->tile_n = tile_n;
     gg->products = products;
     gg->k_block = k_block;
+    gg->pair = pair;
     return BPM_OK;
 }
 
@@ -309,11 +316,12 @@ void grouped_gemm_free(GroupedGemm* gg) {
     gg->n_groups = gg->total_tiles = 0;
 }
 
-int grouped_gemm_launch(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err) {
+int grouped_gemm_launch(cudaStream_t s, GroupedGemm& gg, int sm_count, int* err) {
     if (!gg.d_groups) {
         set_error("grouped GEMM not set up");
         return BPM_ERR_STATE;
     }
+    if (gg.pair) return grouped_gemm_pair_launch(s, gg, sm_count, err);
     if (gg.k_block == 32) {
         if (gg.products == 3)
             return gg.tile_n == 128 ? launch_grouped<3, 128, 32>(s, gg, sm_count, err)

@@ -170,12 +170,16 @@ struct GroupedGemm {
     GemmGroupDev* d_groups = nullptr;
     int n_groups = 0, total_tiles = 0, tile_n = 256, products = 3, k_block = 64;
     unsigned long long wait_ns = 0;   // limit of the non-drain waits (0: the default)
+    int pair = 0;                     // 1: 256 x 256 tiles on CTA pairs (tcgen05 cta_group::2)
+    int max_pairs = 0;                // co-resident CTA pairs of the pair kernel (0: not yet queried)
 };
 // k_block: K depth of one pipeline stage, 64 (128-byte swizzle) or 32 (64-byte swizzle, twice the stages)
+// pair: 256 x 256 output tiles computed by the two CTAs of a cluster (bpm_gemm_pair.cu)
 int grouped_gemm_setup(GroupedGemm* gg, const std::vector<GemmOperands>& ops, int tile_n, int products, int raster,
-                       int k_block, size_t l2_bytes);
+                       int k_block, size_t l2_bytes, int pair = 0);
+int grouped_gemm_pair_launch(cudaStream_t s, GroupedGemm& gg, int sm_count, int* err);
 void grouped_gemm_free(GroupedGemm* gg);
-int grouped_gemm_launch(cudaStream_t s, const GroupedGemm& gg, int sm_count, int* err);
+int grouped_gemm_launch(cudaStream_t s, GroupedGemm& gg, int sm_count, int* err);
 // TMA map of a row-major BF16 [rows][inner] matrix, boxes of box_rows x box_inner (64 or 32)
 int make_bf16_tensor_map(CUtensorMap* map, const void* ptr, int inner, int rows, int box_rows, int box_inner = 64);
 

@@ -5,9 +5,13 @@ Both sides evaluate the same readings in FP64; they differ only in the demag
 matrix (the GPU's batched-CG assembly agrees with the oracle's dense LU to
 about 1e-12 of max|N|, at most 1e-9 by the assembly test), the exchange
 summation (difference form against the dense product) and the order of the
-volume-weighted sums.  A field difference dB moves m by about gamma dB t, so
-over tens of ps the states agree to well below the FP32 path's 1e-6: the bar
-here is 1e-8, and the switch flags and crossing times must agree to 1e-6 ps."""
+volume-weighted sums.  A field difference dB moves m by about gamma dB t; while
+an island reverses, its state passes near the unstable equilibrium, where such
+differences grow about as exp(gamma B_K t) (B_K ~ 2 T: e-folding in ~3 ps).
+Without a reversal the states agree to rounding (1e-14 over 1 ps on the census
+mesh); through one (the 20 ps run) to 1e-6, three orders below the
+mixed-precision bar, while a dropped or mis-signed term moves m by more than
+1e-2.  The switch flags and crossing times must agree to 1e-6 ps."""
 import math
 import os
 
@@ -53,7 +57,7 @@ def test_plain_fp64_trajectory_matches_oracle(ctx, small):
     err = float(np.abs(got["m"].transpose(0, 2, 1) - ref["m"]).max())
     mz_err = float(np.abs(got["m"][:, 2, :] @ (ops.V / ops.V.sum()) - ref["mz"]).max())
     print(f"FP64 plain vs oracle over 20 ps: max |dm| {err:.2e}, <m_z> {mz_err:.2e}")
-    assert err <= 1e-8 and mz_err <= 1e-8
+    assert err <= 1e-6 and mz_err <= 1e-6
     assert got["device_ms"] > 0 and np.all(got["status"] == 0)
     # the state moved well away from the start
     assert float(np.abs(got["m"][:, 2, :] - 1.0).max()) > 0.05
@@ -94,7 +98,7 @@ def test_plain_fp64_census_mesh_matches_oracle(ctx):
     ref = llg.Batch(ops, pick, p, head_map=hm).run()
     err = float(np.abs(got["m"].transpose(0, 2, 1) - ref["m"]).max())
     print(f"census mesh, FP64 plain vs oracle over 1 ps: max |dm| {err:.2e}")
-    assert err <= 1e-8
+    assert err <= 1e-10
 
 
 def test_plain_fp64_needs_the_fp64_operator(ctx):
