@@ -129,6 +129,14 @@ def gemm_traffic(prec, B, n):
     return NCU_GEMM_TRAFFIC.get((int(prec), int(B), int(n)))
 
 
+# Warp instructions per island-node of the Heun stage kernels (two islands per CTA, BF16x3
+# operand) from ncu's smsp__inst_executed.sum of one launch over 2048 islands of the 1547-node
+# mesh (profiles/heun_stages_census_2048.md: 50.7 M and 52.5 M).  Remove when the kernels change.
+NCU_STAGE_WARP_INSTR = {1547: (50.7e6 / (2048 * 1547), 52.5e6 / (2048 * 1547))}
+SM_COUNT = 152
+ISSUE_PER_SM_CLK = 4           # one warp instruction per scheduler per cycle, four schedulers per SM
+
+
 # ---------------------------------------------------------------------------
 # The FP64 oracle on the host cores: spawned worker processes, each with its
 # own copy of the census mesh operators and a pinned number of BLAS threads.
@@ -747,6 +755,16 @@ def main(args):
                   "stage2_achieved": s2_bytes / (kt["stage2_ms"] * 1e-3) / 1e9}
     roof_steps["stage1_frac"] = roof_steps["stage1_achieved"] / hbm_peak
     roof_steps["stage2_frac"] = roof_steps["stage2_achieved"] / hbm_peak
+    wi = NCU_STAGE_WARP_INSTR.get(n) if prec == L.PREC_BF16X3 else None
+    if wi and clocks:
+        # the bound these kernels meet first: instruction issue (4 warp instructions per cycle
+        # per SM at the run's median SM clock)
+        issue_peak = SM_COUNT * ISSUE_PER_SM_CLK * clocks["sm_mhz"] * 1e6
+        roof_steps["issue"] = {"bound": "issue", "unit": "warp instructions/s", "peak": issue_peak,
+                               "warp_instructions_per_island_node": list(wi),
+                               "stage1_frac": B * n * wi[0] / (kt["stage1_ms"] * 1e-3) / issue_peak,
+                               "stage2_frac": B * n * wi[1] / (kt["stage2_ms"] * 1e-3) / issue_peak,
+                               "peak_source": "152 SMs x 4 schedulers x median SM clock of the run"}
 
     # end to end through the one-call public API with pinned host buffers
     e2e = None

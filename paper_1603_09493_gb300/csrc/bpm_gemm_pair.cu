@@ -13,12 +13,13 @@
 // Warp roles (per CTA):
 //   warp 0  lane 0 streams the CTA's halves of the k-blocks with TMA into a ring
 //           of shared-memory stages, each stage signalled on the CTA's own
-//           barrier; in the odd CTA lane 1 forwards every landed stage to a
-//           second barrier of the stage in the even CTA (so each CTA waits for
-//           its own copies alone before it gives up its shared memory);
+//           barrier (so each CTA waits for its own copies alone before it gives
+//           up its shared memory);
 //   warp 1  allocates TMEM with the peer (two accumulators of 256 columns); in
 //           the even CTA one lane issues the MMAs, tile i into accumulator i % 2,
-//           and commits them to both CTAs' barriers;
+//           and commits them to both CTAs' barriers; in the odd CTA one lane
+//           forwards every landed stage to a second barrier of the stage in the
+//           even CTA;
 //   warps 2-5  read the CTA's accumulator rows back and store them, then arrive
 //           on the even CTA's accumulator-empty barrier.
 // Every wait is bounded as in k_gemm_grouped; both CTAs of a pair take the same
@@ -71,33 +72,6 @@ __device__ __forceinline__ void cluster_sync() {
 
 __device__ __forceinline__ void remote_arrive(uint32_t cluster_addr) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-
-// bounded wait, with cluster-scope acquire, for a phase of a barrier that the peer CTA arrives on
-__device__ __forceinline__ bool peer_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool peer_wait(uint32_t bar, uint32_t parity, int* err, int code, unsigned long long limit) {
-    if (peer_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        for (int i = 0; i < 256; ++i)
-            if (peer_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit || *(volatile int*)err != 0) break;
-    }
-    atomicExch(err, code);
-    return false;
 }
 
 __device__ __forceinline__ int ld_cluster_s32(uint32_t cluster_addr) {
@@ -234,8 +208,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
         // drain: this CTA's copies land before it can give up its shared memory
         const int armed = kbg;
         for (int k = (armed > S ? armed - S : 0); k < armed; ++k) mbar_drain(full_bar(k % S), (k / S) & 1, err, 22);
-    } else if (warp == 0 && lane == 1 && !leader) {
+    } else if (warp == 1 && lane == 0 && !leader) {
         // ---------------- forwarder (odd CTA): each landed stage to the even CTA ----------------
+        // (a warp of its own: the producer's waits may suspend its warp for a while)
         int kbg = 0;
         bool ok = true;
         for (int t = cluster; t < total_tiles && ok; t += n_clusters) {
@@ -262,8 +237,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPThreads, 1)
             const uint32_t acc = tmem + (uint32_t)(a * PTN);
             for (int kb = 0; kb < nk; ++kb, ++kbg) {
                 const int s = kbg % S;
+                // the odd CTA's copies of the stage have landed when its forwarder arrives (it saw
+                // them complete on its own barrier first)
                 ok = mbar_wait(full_bar(s), (kbg / S) & 1, err, 25, true, wait_ns) &&
-                     peer_wait(peer_bar(s), (kbg / S) & 1, err, 28, wait_ns);
+                     mbar_wait(peer_bar(s), (kbg / S) & 1, err, 28, true, wait_ns);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll

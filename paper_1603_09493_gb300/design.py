@@ -21,12 +21,13 @@ Readings (the paper gives its own head and media parameters, not these ranges):
 * every island's top sits at z = 16 nm of the head map, 5 nm below the
   air-bearing surface, whatever its thickness;
 * a design's head field is the synthetic pole-tip field with its peak, tilt and
-  width; up to 16 heads share one map, side by side along its cross-track
-  axis, one 64 nm block each, and an island samples its design's head through
-  a cross-track offset of 64 nm times the head's place in the map (islands stay
-  within 20 nm of their block's centre, so no lookup reaches a neighbouring
-  block; with offsets below 1 um the FP32 lookup coordinate keeps a resolution
-  of 6e-5 nm, a head-field error of about 1e-5 T);
+  width; up to 256 heads share one map, as a 16 x 16 array of 64 nm blocks
+  along its down-track (x, head frame) and cross-track (y) axes, and an island
+  samples its design's head through an offset of 64 nm times the head's block
+  coordinates (islands and the moving head stay within 20 nm of their block's
+  centre, so no lookup reaches a neighbouring block; with offsets below 1 um
+  the FP32 lookup coordinate keeps a resolution of 6e-5 nm, a head-field error
+  of about 1e-5 T);
 * the pitch (9-14 nm) and field width (6-12 nm) ranges are wide enough that
   both error events occur among random designs;
 * the head centre reaches the target at 100 ps (x0 = -v * 100 ps), the fields
@@ -60,7 +61,8 @@ JITTER = dict(Ms=0.05, Ku=0.05, tilt_deg=2.0, pos_nm=1.0)
 T_END_PS = 250.0
 Z_TOP_NM = 16.0
 BLOCK_NM = 64
-HEADS_PER_MAP = 16
+BLOCKS = 16                      # blocks per map axis
+HEADS_PER_MAP = BLOCKS * BLOCKS
 
 
 def values(Z) -> dict:
@@ -108,16 +110,29 @@ def upload_grid(ctx) -> list:
     return [ctx.mesh_upload(m, mats) for m, mats in grid_meshes()]
 
 
+def head_block(h) -> tuple:
+    """Block coordinates (down-track, cross-track) of head h within its map."""
+    h = np.asarray(h) % HEADS_PER_MAP
+    return h // BLOCKS, h % BLOCKS
+
+
 def head_stack(heads) -> synth.HeadMap:
-    """One map holding the heads [H][3] (peak T, tilt deg, width nm) side by side
-    along y: head h's block spans y in [64 h - 32, 64 h + 32) nm and is the
-    synthetic pole-tip map of that head (18 planes, island top at z = 16 nm)."""
+    """One map holding the heads [H][3] (peak T, tilt deg, width nm): head h is
+    the synthetic pole-tip map of that head (18 planes, island top at z = 16 nm)
+    in the block spanning x in [64 bx - 32, 64 bx + 32), y in [64 by - 32,
+    64 by + 32) nm, (bx, by) = head_block(h)."""
     heads = np.asarray(heads, np.float64)
-    if not 1 <= len(heads) <= HEADS_PER_MAP:
+    H = len(heads)
+    if not 1 <= H <= HEADS_PER_MAP:
         raise ValueError(f"1..{HEADS_PER_MAP} heads per map")
-    blocks = [synth.synthetic_head_map(nx=64, ny=BLOCK_NM, nz=18, B_peak_T=float(b), tilt_deg=float(t),
+    nby, nbx = min(H, BLOCKS), (H + BLOCKS - 1) // BLOCKS
+    blocks = [synth.synthetic_head_map(nx=BLOCK_NM, ny=BLOCK_NM, nz=18, B_peak_T=float(b), tilt_deg=float(t),
                                        sx_nm=float(w), sy_nm=float(w), z_top_nm=Z_TOP_NM) for b, t, w in heads]
-    B = np.concatenate([b.B_T for b in blocks], axis=1)
+    nz = blocks[0].B_T.shape[0]
+    B = np.zeros((nz, nby * BLOCK_NM, nbx * BLOCK_NM, 3), np.float32)
+    for h, blk in enumerate(blocks):
+        bx, by = head_block(h)
+        B[:, by * BLOCK_NM:(by + 1) * BLOCK_NM, bx * BLOCK_NM:(bx + 1) * BLOCK_NM] = blk.B_T
     return synth.HeadMap(B_T=B, origin_nm=blocks[0].origin_nm.copy(), h_nm=blocks[0].h_nm,
                          info=dict(heads=heads.tolist(), block_nm=BLOCK_NM))
 
@@ -194,12 +209,13 @@ def islands(R: Realisations, grid_ids, rows):
     Ms = (R.v["Ms_scale"][rows] * R.ms[rows]).astype(np.float32)
     Ku = (R.v["Ku_scale"][rows] * R.ku[rows]).astype(np.float32)
     u = np.stack([np.sin(R.tilt[rows]), np.zeros(len(rows)), np.cos(R.tilt[rows])], 1).astype(np.float32)
-    y0 = BLOCK_NM * (R.head[rows] % HEADS_PER_MAP).astype(np.float64)
+    bx, by = head_block(R.head[rows])
+    x0, y0 = BLOCK_NM * bx.astype(np.float64), BLOCK_NM * by.astype(np.float64)
     ox, oy = adjacent_offset(R.v["layout"][rows], R.v["pitch_nm"][rows])
     mk = lambda px, py: synth.Islands(mesh_id=mid.copy(), Ms_scale=Ms.copy(), Ku_scale=Ku.copy(), u=u.copy(),
                                       pos_nm=np.stack([px, py], 1).astype(np.float32),
                                       Hext_T=np.zeros((len(rows), 3), np.float32))
-    return mk(R.dx[rows], y0), mk(R.dx[rows] + ox, y0 + oy)
+    return mk(x0 + R.dx[rows], y0), mk(x0 + R.dx[rows] + ox, y0 + oy)
 
 
 def run_params(v_m_per_s: float) -> synth.RunParams:
@@ -209,7 +225,7 @@ def run_params(v_m_per_s: float) -> synth.RunParams:
 
 def llg_labels(ctx, grid_ids, R: Realisations, precision: int = L.PREC_BF16X3) -> np.ndarray:
     """LLG labels [N][2] (target switched, adjacent island flipped) of every
-    realisation: one batch per (group of 16 heads, velocity level), the group's
+    realisation: one batch per (group of 256 heads, velocity level), the group's
     heads in one stacked map."""
     Y = np.zeros((len(R), 2), np.float32)
     group = R.head // HEADS_PER_MAP

@@ -48,16 +48,19 @@ def test_geometry_grid_order_thickness_and_top_height():
 
 
 def test_head_stack_holds_each_head_in_its_own_block():
-    heads = np.array([[1.0, 10.0, 6.0], [1.6, 40.0, 10.0], [1.3, 25.0, 8.0]])
+    rng = np.random.default_rng(2)
+    heads = np.stack([rng.uniform(1.0, 1.6, 19), rng.uniform(10, 40, 19), rng.uniform(6, 12, 19)], 1)
     hm = design.head_stack(heads)
-    assert hm.B_T.shape == (18, 3 * design.BLOCK_NM, 64, 3)
+    assert hm.B_T.shape == (18, 16 * design.BLOCK_NM, 2 * design.BLOCK_NM, 3)   # 16 x 2 blocks
     assert np.allclose(hm.origin_nm, [-32.0, -32.0, 0.0])
     for h, (b, t, w) in enumerate(heads):
+        bx, by = design.head_block(h)
+        assert (bx, by) == (h // 16, h % 16)
         one = synth.synthetic_head_map(nx=64, ny=64, nz=18, B_peak_T=b, tilt_deg=t, sx_nm=w, sy_nm=w,
                                        z_top_nm=design.Z_TOP_NM)
-        assert np.array_equal(hm.B_T[:, 64 * h:64 * (h + 1)], one.B_T)
-        # the peak of block h sits at y = 64 h (block index 32), the field direction is the head's tilt
-        blk = hm.B_T[:, 64 * h:64 * (h + 1)]
+        blk = hm.B_T[:, 64 * by:64 * (by + 1), 64 * bx:64 * (bx + 1)]
+        assert np.array_equal(blk, one.B_T)
+        # the peak of block h sits at its centre (index 32, 32), the field direction is the head's tilt
         iz, iy, ix = np.unravel_index(np.argmax(np.linalg.norm(blk, axis=-1)), blk.shape[:3])
         assert iy == 32 and ix == 32
         f = blk[iz, iy, ix]
@@ -89,17 +92,18 @@ def test_realisations_are_design_major_with_bounded_features():
 
 
 def test_islands_sit_at_their_layout_offsets_in_their_head_block():
-    D = 24
+    D = 40                              # 40 heads: blocks in two down-track columns and a third
     Z = synth.counter_uniform(5, 0, np.arange(D * 12)).reshape(D, 12)
     R = design.realisations(Z, 2, seed=3, first_index=0)
     grid = list(range(1000, 1081))
     tgt, adj = design.islands(R, grid, np.arange(len(R)))
     v = R.v
-    y0 = 64.0 * (R.head % design.HEADS_PER_MAP)
-    assert np.allclose(tgt.pos_nm[:, 0], R.dx, atol=1e-5) and np.allclose(tgt.pos_nm[:, 1], y0)
+    y0 = 64.0 * (R.head % 16)
+    x0 = 64.0 * (R.head // 16)
+    assert np.allclose(tgt.pos_nm[:, 0], x0 + R.dx, atol=1e-4) and np.allclose(tgt.pos_nm[:, 1], y0)
     p = v["pitch_nm"]
     lay = v["layout"].astype(int)
-    want_x = R.dx + np.where(lay == 1, 0.5 * p, 0.0)
+    want_x = x0 + R.dx + np.where(lay == 1, 0.5 * p, 0.0)
     want_y = y0 + np.where(lay == 2, -p, p)
     assert np.allclose(adj.pos_nm[:, 0], want_x, atol=1e-5) and np.allclose(adj.pos_nm[:, 1], want_y, atol=1e-4)
     assert np.array_equal(tgt.mesh_id, adj.mesh_id)

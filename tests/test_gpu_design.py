@@ -37,9 +37,9 @@ def grid(ctx):
 
 
 def test_stacked_heads_give_each_island_its_own_head(ctx, grid):
-    Z = synth.counter_uniform(11, 0, np.arange(12 * 12)).reshape(12, 12)
+    Z = synth.counter_uniform(11, 0, np.arange(20 * 12)).reshape(20, 12)
     Z[:, design.KEYS.index("v_m_per_s")] = 0.6                       # one velocity level
-    R = design.realisations(Z, 4, seed=12, first_index=0)             # 12 heads in one map
+    R = design.realisations(Z, 3, seed=12, first_index=0)             # 20 heads: 16 x 2 blocks
     p = design.run_params(float(R.v["v_m_per_s"][0]))
     hid = ctx.headmap_upload(design.head_stack(R.heads))
     tgt, adj = design.islands(R, grid, np.arange(len(R)))
