@@ -469,7 +469,10 @@ def measure_search(ctx, generations=8, population=256, top_k=16, n_jit_screen=64
                               n_jitter_screen=n_jit_screen, n_jitter_verify=n_jit_verify, seed=43)
     res = design.search(ctx, sur, grid, cfg)
     sur.destroy()
+    # the paper's write error rates (Eqs. 1-2, critical-field search) of the final elites
+    ranked = design.rank_by_ber(ctx, grid, res.elite_Z)
     best = design.values(res.best_Z[None])
+    best_ber = design.values(ranked["best_Z"][None])
     loop_s = res.screen_s + res.verify_s
     return {"problem": "12 design parameters (diameter, t_soft, t_hard, Ms, Ku, interlayer exchange, pitch, "
                        "layout, head peak, tilt, width, velocity) + 4 jitter values; labels: target switched, "
@@ -479,6 +482,12 @@ def measure_search(ctx, generations=8, population=256, top_k=16, n_jit_screen=64
             "n_jitter_screen": n_jit_screen, "n_jitter_verify": n_jit_verify,
             "best_design": {k: float(v[0]) for k, v in best.items()},
             "best_write_error_rate": float(res.best_rates[0]), "best_adjacent_flip_rate": float(res.best_rates[1]),
+            "elites_by_ber": {"ber_targ": ranked["ber_targ"].tolist(), "ber_prev": ranked["ber_prev"].tolist(),
+                              "best_ber_targ_plus_prev": float(ranked["ber_sum"][ranked["best"]]),
+                              "best_design": {k: float(v[0]) for k, v in best_ber.items()},
+                              "llg_runs": int(ranked["runs"]), "seconds": ranked["seconds"],
+                              "method": "critical-field search of Sec. II.C on each elite's nominal island under "
+                                        "its head, sigma = 0.015 H_A, BER = erfc(H_crit / (sqrt 2 sigma)) / 2"},
             "best_per_generation": [h["best_verified"] for h in res.history],
             "train_labels_s": label_s, "train_s": train_s, "screen_s": res.screen_s, "verify_s": res.verify_s,
             "llg_only_s": res.llg_only_s, "loop_vs_llg_only": res.llg_only_s / loop_s,
@@ -699,7 +708,11 @@ def main(args):
     p.substeps = k
     bt = ctx.batch(isl, p, precision=prec, map_id=hid)
     tuning = None
-    if not args.no_autotune:
+    if args.gemm_pair:
+        # the CTA-pair demag GEMM (256 x 256 tiles on two SMs), its fastest k-block
+        bt.set_tuning(256, 256, L.RASTER_AUTO, 2, 64, gemm_pair=1)
+        tuning = {"gemm_pair": 1, "gemm_k_block": 64, "cached": False}
+    elif not args.no_autotune:
         tuning = bt.autotune_cached(os.path.expanduser("~/.cache/bpmllg/tuning.json"),
                                     torch.cuda.get_device_name(), reps=4)
         bt.set_state(None, 0.0)
@@ -829,6 +842,7 @@ if __name__ == "__main__":
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--gemm-pair", action="store_true", help="run the demag GEMM on CTA pairs (no autotune)")
     ap.add_argument("--workload", default="census",
                     choices=["census", "uneven", "extras", "surrogate", "surrogate-study"])
     ap.add_argument("--study-round", type=int, default=32768, help="labels per round of the surrogate study")

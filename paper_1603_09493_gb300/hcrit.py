@@ -60,7 +60,8 @@ def _with_field(isl: Islands, idx, H: np.ndarray) -> Islands:
 
 def critical_field_search(run_flags, islands: Islands, direction: np.ndarray, sigma_T: np.ndarray,
                           role: str, levels: int = 3, step: float = 0.5, top: float = 4.0) -> SearchResult:
-    """run_flags(Islands) -> switched flags [B] (one batch of LLG runs).
+    """run_flags(Islands, designs) -> switched flags [B] (one batch of LLG runs);
+    designs [B] holds the design index of every island of the batch.
 
     islands: one island per design (its position is the bit's position);
     direction: [D][3] unit head-field direction; sigma_T: [D]; role 'targ'
@@ -75,7 +76,7 @@ def critical_field_search(run_flags, islands: Islands, direction: np.ndarray, si
     idx = np.repeat(np.arange(D), G)
     mult = np.tile(grid, D)
     H = sign * (mult * sigma_T[idx])[:, None] * direction[idx]
-    sw = np.asarray(run_flags(_with_field(islands, idx, H)), bool).reshape(D, G)
+    sw = np.asarray(run_flags(_with_field(islands, idx, H), idx), bool).reshape(D, G)
     good = sw if role == "targ" else ~sw
     runs = D * G
     aborted = ~good[:, 0]
@@ -96,7 +97,7 @@ def critical_field_search(run_flags, islands: Islands, direction: np.ndarray, si
             break
         mid = 0.5 * (lo[active] + hi[active])
         Hm = sign * (mid * sigma_T[active])[:, None] * direction[active]
-        swm = np.asarray(run_flags(_with_field(islands, active, Hm)), bool)
+        swm = np.asarray(run_flags(_with_field(islands, active, Hm), active), bool)
         gm = swm if role == "targ" else ~swm
         runs += active.size
         lo[active] = np.where(gm, mid, lo[active])
@@ -108,6 +109,6 @@ def critical_field_search(run_flags, islands: Islands, direction: np.ndarray, si
 
 def gpu_flag_runner(ctx, params, n_intervals: int, map_id: int = -1, precision: int = L.PREC_BF16X3):
     """run_flags for critical_field_search on the batched GPU path."""
-    def run(isl: Islands):
+    def run(isl: Islands, designs=None):
         return ctx.run_batch(isl, params, n_intervals, precision=precision, map_id=map_id)["switched"]
     return run

@@ -20,7 +20,14 @@ for these runs, more than a test may take, so its results are stored:
               the switch flag, first crossing time and final volume-averaged
               m_z of every island.
 
-  python tests/golden/make_headline_golden.py census|outcomes [--workers N]
+  design-ber  tests/golden/design_ber.npz
+              the critical-field search of Sec. II.C (Eqs. 1-2) for the three
+              designs of design_inputs.parity_designs, both roles (target and
+              previous bit), each design under its own head in one stacked
+              map, with the step count of the strongest constant field of the
+              grid: the critical fields, error rates and aborts.
+
+  python tests/golden/make_headline_golden.py census|outcomes|design-ber [--workers N]
 """
 from __future__ import annotations
 
@@ -98,6 +105,22 @@ def _outcome_chunk(args):
     return r["switched"], r["t_sw"], r["mz"], r["status"]
 
 
+def _design_ber_one(args):
+    d, role, k = args
+    from oracle import fem
+    from oracle import hcrit as ohcrit
+    from paper_1603_09493_gb300 import design_inputs as DI
+    Z = DI.parity_designs()
+    tgt, direction, sigma, R = DI.critical_field_inputs(Z, role)
+    mesh, mats = DI.grid_meshes()[int(tgt.mesh_id[0])]
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats)
+    p = DI.run_params(float(R.v["v_m_per_s"][0]))
+    p.substeps = k
+    hm = DI.head_stack(R.heads)
+    h, ber, ab = ohcrit.search(ops, tgt.subset([d]), p, direction[d:d + 1], sigma[d:d + 1], role, head_map=hm)
+    return float(h[0]), float(ber[0]), bool(ab[0])
+
+
 def _pool(workers):
     # one BLAS thread per worker process; spawned, so that no parent state is forked
     os.environ["OMP_NUM_THREADS"] = "1"
@@ -153,9 +176,34 @@ def make_outcomes(workers: int):
     print(f"outcomes: k={k}, {sw.sum()} of {sw.size} switched, {time.time() - t:.0f} s -> {out}")
 
 
+def make_design_ber(workers: int):
+    from oracle import fem, llg
+    from paper_1603_09493_gb300 import design_inputs as DI
+    Z = DI.parity_designs()
+    tgt, direction, sigma, R = DI.critical_field_inputs(Z, "targ")
+    assert len(set(tgt.mesh_id.tolist())) == 1 and len(set(R.v["v_m_per_s"].tolist())) == 1
+    mesh, mats = DI.grid_meshes()[int(tgt.mesh_id[0])]
+    ops = fem.MeshOperators(mesh.xyz_nm, mesh.tets, mesh.tet_region, mats, with_demag=False)
+    probe = tgt.subset(np.arange(len(tgt)))
+    probe.Hext_T = (4.0 * sigma[:, None] * direction).astype(np.float32)
+    p = DI.run_params(float(R.v["v_m_per_s"][0]))
+    k = llg.stable_substeps(llg.Batch(ops, probe, p, head_map=DI.head_stack(R.heads), demag=np.zeros((1, 1))))
+    tasks = [(d, role, k) for role in ("targ", "prev") for d in range(len(Z))]
+    t = time.time()
+    with _pool(min(workers, len(tasks))) as pool:
+        res = pool.map(_design_ber_one, tasks)
+    h = np.array([r[0] for r in res]).reshape(2, len(Z))
+    ber = np.array([r[1] for r in res]).reshape(2, len(Z))
+    ab = np.array([r[2] for r in res]).reshape(2, len(Z))
+    out = os.path.join(GOLDEN, "design_ber.npz")
+    np.savez_compressed(out, k=k, roles=np.array(["targ", "prev"]), h_crit_T=h, ber=ber, aborted=ab, sigma_T=sigma,
+                        Z=Z)
+    print(f"design-ber: k={k}, H_crit/sigma {h / sigma[None, :]}, {time.time() - t:.0f} s -> {out}")
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["census", "outcomes"])
+    ap.add_argument("what", choices=["census", "outcomes", "design-ber"])
     ap.add_argument("--workers", type=int, default=os.cpu_count() or 1)
     a = ap.parse_args()
-    (make_census if a.what == "census" else make_outcomes)(a.workers)
+    {"census": make_census, "outcomes": make_outcomes, "design-ber": make_design_ber}[a.what](a.workers)

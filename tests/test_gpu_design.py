@@ -103,3 +103,31 @@ def test_surrogate_on_the_design_problem(ctx, grid):
         assert counted[pick].sum(1).mean() < counted[rnd].sum(1).mean()
     finally:
         sur.destroy()
+
+
+def test_critical_field_ber_of_designs_matches_oracle(ctx, grid):
+    # the write and previous-bit BERs (Sec. II.C, Eqs. 1-2) of three designs that share a mesh
+    # and a velocity level, each under its own head in one stacked map: the library's
+    # critical-field search against the oracle's (stored by tests/golden/make_headline_golden.py
+    # design-ber) on the same islands, map and step count; both take every decision from switch
+    # outcomes, so the critical fields agree to one finest-grid step sigma/8
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    ref = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "design_ber.npz"))
+    Z = design.parity_designs()
+    assert np.allclose(Z, ref["Z"])
+    k = int(ref["k"])
+    for r, role in enumerate(("targ", "prev")):
+        tgt, direction, sigma, R = design.critical_field_inputs(Z, role)
+        assert np.allclose(sigma, ref["sigma_T"], rtol=1e-12)
+        if role == "targ":      # the library's count for the strongest field of the grid is the oracle's
+            probe = tgt.subset(np.arange(3))
+            probe.mesh_id = np.asarray(grid, np.int32)[probe.mesh_id]
+            probe.Hext_T = (4.0 * sigma[:, None] * direction).astype(np.float32)
+            hid = ctx.headmap_upload(design.head_stack(R.heads))
+            assert ctx.stable_substeps(probe, design.run_params(float(R.v["v_m_per_s"][0])), hid)[0] == k
+        got = design.critical_field_ber(ctx, grid, Z, role, precision=L.PREC_BF16X3, substeps=k)
+        print(role, "gpu H_crit/sigma", got.h_crit_T / sigma, "BER", got.ber,
+              "oracle", ref["h_crit_T"][r] / sigma, ref["ber"][r])
+        assert np.array_equal(got.aborted, ref["aborted"][r])
+        assert np.all(np.abs(got.h_crit_T - ref["h_crit_T"][r]) <= sigma / 8 + 1e-12)

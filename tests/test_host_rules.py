@@ -86,7 +86,8 @@ def test_critical_field_search_matches_the_oracle_search(monkeypatch):
 
         monkeypatch.setattr(ohcrit, "Batch", FakeBatch)
         h_o, ber_o, ab_o = ohcrit.search(None, isl, None, direction, sigma, role)
-        res = hcrit.critical_field_search(lambda sub: _threshold_rule(sub, role), isl, direction, sigma, role)
+        res = hcrit.critical_field_search(lambda sub, designs: _threshold_rule(sub, role), isl, direction, sigma,
+                                          role)
         assert np.array_equal(res.aborted, ab_o) and np.array_equal(res.h_crit_T, h_o)
         # the same Gaussian tail, erfc on one side and 1 - erf on the other: equal up to the
         # cancellation of 1 - erf at 4 sigma (~3e-12 relative)

@@ -71,9 +71,9 @@ def _functions_importing_the_oracle(path):
 
 def test_bench_and_smoke_reach_the_oracle_only_from_their_baseline_legs():
     bench = _functions_importing_the_oracle(os.path.join(ROOT, "bench.py"))
-    # oracle_ops / run_oracle_sample serve cpu_baseline; measure_neb / measure_ego time their own
-    # oracle baselines; main_reference is the reference arm
-    assert bench <= {"cpu_baseline", "oracle_ops", "run_oracle_sample", "measure_neb", "measure_ego",
-                     "main_reference"}, bench
+    # the worker-pool functions and oracle_step_count serve cpu_baseline and the reference arm
+    # (main_reference); measure_neb / measure_ego time their own oracle baselines
+    assert bench <= {"cpu_baseline", "_oracle_worker_init", "_oracle_worker_run", "oracle_step_count",
+                     "measure_neb", "measure_ego", "main_reference"}, bench
     entry = _functions_importing_the_oracle(os.path.join(ROOT, "__graft_entry__.py"))
     assert entry <= {"smoke", "_smoke_surrogate"}, entry
