@@ -236,11 +236,17 @@ def nominal(Z) -> Realisations:
 
 def parity_designs() -> np.ndarray:
     """Three designs that share the grid's middle geometry (d 8 nm, soft 3 nm, hard 7 nm,
-    exchange scale 0.3) and one velocity level, with their own Ms, Ku, pitch, layout and
-    heads: the cases whose critical-field bit-error rates are compared with the oracle's."""
-    Z = synth.counter_uniform(61, 0, np.arange(3 * 12)).reshape(3, 12)
+    exchange scale 0.3), one velocity level, a 12 nm head field width and a 9 nm pitch, with
+    their own Ms, Ku, layout, tilt and head peaks of 1.05, 1.14 and 1.19 T: their critical
+    fields lie inside the search grid (the write margin of the first, the previous-bit margins
+    of the other two), the cases whose critical-field bit-error rates are compared with the
+    oracle's."""
+    Z = synth.counter_uniform(61, 0, np.arange(6 * 12)).reshape(6, 12)[[1, 3, 4]]
     for key in GEOMETRY_KEYS + ("v_m_per_s",):
         Z[:, KEYS.index(key)] = 0.5
+    Z[:, KEYS.index("B_peak_T")] = [0.08, 0.24, 0.32]
+    Z[:, KEYS.index("width_nm")] = 1.0
+    Z[:, KEYS.index("pitch_nm")] = 0.0
     return Z
 
 
