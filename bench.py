@@ -362,6 +362,39 @@ def measure_neb(ctx, mid, hm, hid, D=64, P=16, iters=400, mesh=None, mats=None):
                     "wall-clock incl. buffer setup and convergence checks every 50 updates"}
 
 
+def measure_head_field(ctx, nx=64, ny=64, nz=18, reps=20):
+    """The head-field solve of the saturated main pole (Table I's initial design) on a head map
+    of the census frame, written to device memory; CUDA events on the context stream."""
+    import torch
+    from paper_1603_09493_gb300 import synth
+    g = synth.pole_geometry(z_abs_nm=18.0, z_sul_nm=-2.0)
+    out = torch.empty((nz, ny, nx, 3), dtype=torch.float32, device="cuda")
+    org = (-48.0, -32.0, 0.0)
+    ctx.head_field(g, nx, ny, nz, 1.0, org, out=out)
+    stream = torch.cuda.ExternalStream(ctx.stream_ptr)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.head_field(g, nx, ny, nz, 1.0, org, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    B = out.cpu().numpy()
+    # the oracle's quadrature on a bounded sample of voxels
+    from oracle import polefield
+    pts = np.array([[-10.0, 0.0, 17.0], [0.0, 7.0, 17.0], [-30.0, 20.0, 5.0], [5.0, -10.0, 12.0]])
+    t = time.perf_counter()
+    polefield.field(g, pts)
+    o_vox = len(pts) / (time.perf_counter() - t)
+    return {"voxels": nx * ny * nz, "ms_per_map": ms, "voxels_per_s": nx * ny * nz / (ms * 1e-3),
+            "triangles": 24, "peak_under_pole_T": float(B[17, 32, 38, 2]),
+            "form": "saturated CoFe main pole (Table I initial design) as surface charges, charge sheet at the "
+                    "yoke edge, under-layer image; closed form per triangle, FP64, one thread per voxel",
+            "cpu_baseline": {"voxels_per_s": o_vox, "kind": "oracle", "cores": 1,
+                             "sample": f"{len(pts)} voxels, adaptive Gauss-Legendre quadrature of the same charges"}}
+
+
 def measure_ego(ctx, n=240, d=12, T=256, N=1 << 20):
     """EGO steps on the GPU (Sec. II.A) at the paper's scale of ten or more training
     designs per parameter: a batch of T likelihood evaluations (one Cholesky each)
@@ -814,6 +847,7 @@ def main(args):
         extras["neb"] = measure_neb(ctx, mid, hm, hid, mesh=None if args.no_cpu else mesh,
                                     mats=None if args.no_cpu else mats)
         extras["ego"] = measure_ego(ctx)
+        extras["head_field"] = measure_head_field(ctx)
         extras["search"] = measure_search(ctx)
     ctx.close()
     if rank != 0:

@@ -176,6 +176,54 @@ int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, i
                        float h_nm, const float origin_nm[3], int32_t* map_id_out);
 
 /* ---------------------------------------------------------------------- */
+/* Head field of a saturated main pole (Sec. II.A head model, Table I)     */
+/* ---------------------------------------------------------------------- */
+
+/* Main-pole geometry and the frame of the field map.  Axes as in a head map:
+ * x down-track (the trailing edge of the pole at x = 0 on the ABS), y
+ * cross-track (pole centred at y = 0), z up (nm).  The pole rises from the
+ * air-bearing surface z = z_abs_nm to the yoke edge z_abs_nm + yoke_edge_nm.
+ * Its ABS footprint is a trapezoid: width pole_tip_width_nm at the trailing
+ * edge, narrowing towards the leading edge at the taper angle (measured from
+ * the trailing edge), abs_thickness_nm deep down-track (the leading width is
+ * kept at least a tenth of the trailing width).  The trailing face leans
+ * down-track by the trailing edge angle and the two side faces flare
+ * cross-track by the side edge angle, both from the vertical; the leading face
+ * is vertical.  The side faces are not planar (the taper), so every face is
+ * split into two triangles, the side faces along the diagonal from their
+ * trailing corner at the ABS. */
+typedef struct {
+    float pole_tip_width_nm;       /* Table I: 5 .. 20 nm */
+    float trailing_edge_angle_deg; /* Table I: 5 .. 45 deg */
+    float side_edge_angle_deg;     /* Table I: 5 .. 45 deg */
+    float taper_angle_deg;         /* Table I: 75 deg */
+    float abs_thickness_nm;        /* down-track depth of the ABS footprint */
+    float yoke_edge_nm;            /* height of the yoke edge above the ABS (153 nm) */
+    float Js_T;                    /* saturation polarisation of the pole (CoFe: 2.4 T) */
+    float z_abs_nm;                /* ABS height in the map frame */
+    float z_sul_nm;                /* upper surface of the soft under-layer, below the map */
+    int32_t sul_image;             /* 1: mirror the pole in the under-layer; 0: no under-layer */
+    float reserved[2];
+} bpm_pole_geometry;
+
+/* Field mu0*H (tesla) of the saturated main pole on a voxel grid: the pole is
+ * uniformly magnetised at Js along -z, so its field is that of the magnetic
+ * surface charges Js n_z on its faces (the face at the yoke edge is the charge
+ * sheet that stands in for the yoke, return pole and coil); a soft under-layer
+ * of unbounded permeability is the pole's mirror image in z = z_sul_nm with
+ * charges of the opposite sign.  Each triangle's field is evaluated in closed
+ * form (its solid angle along the normal plus a logarithm per edge) in FP64.
+ * Shields are not modelled.
+ *   B_T  [nz][ny][nx][3] float32: voxel (ix, iy, iz) at origin + h (ix, iy, iz);
+ *        host memory, or device memory of the context when on_device is 1
+ *        (written in stream order on the context stream)
+ * BPM_ERR_ARG for a bad geometry (non-positive sizes or Js, angles outside
+ * [0, 80) deg, a taper outside (0, 90] deg, z_sul above the ABS) or a grid
+ * that reaches the ABS or, with the image, the under-layer. */
+int bpm_head_field_solve(bpm_ctx* ctx, const bpm_pole_geometry* g, int32_t nx, int32_t ny, int32_t nz,
+                         float h_nm, const float origin_nm[3], float* B_T, int on_device);
+
+/* ---------------------------------------------------------------------- */
 /* Batched LLG (Sec. II.C recording simulations, one batch of islands)     */
 /* ---------------------------------------------------------------------- */
 

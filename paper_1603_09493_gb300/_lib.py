@@ -68,6 +68,13 @@ class bpm_neb_params(ctypes.Structure):
                 ("uniform_T", c_double * 3)]
 
 
+class bpm_pole_geometry(ctypes.Structure):
+    _fields_ = [("pole_tip_width_nm", c_float), ("trailing_edge_angle_deg", c_float),
+                ("side_edge_angle_deg", c_float), ("taper_angle_deg", c_float), ("abs_thickness_nm", c_float),
+                ("yoke_edge_nm", c_float), ("Js_T", c_float), ("z_abs_nm", c_float), ("z_sul_nm", c_float),
+                ("sul_image", c_int32), ("reserved", c_float * 2)]
+
+
 class bpm_tuning(ctypes.Structure):
     _fields_ = [("gemm_tile_n", c_int32), ("stage_threads", c_int32), ("gemm_raster", c_int32), ("stage_islands", c_int32),
                 ("gemm_k_block", c_int32), ("gemm_pair", c_int32),
@@ -88,6 +95,8 @@ PROTOTYPES = {
                                 c_uint32, POINTER(c_int32)]),
     "bpm_mesh_info_get": (c_int, [c_void_p, c_int32, POINTER(bpm_mesh_info)]),
     "bpm_mesh_get_operator": (c_int, [c_void_p, c_int32, c_int32, c_void_p]),
+    "bpm_head_field_solve": (c_int, [c_void_p, POINTER(bpm_pole_geometry), c_int32, c_int32, c_int32, c_float,
+                                     c_void_p, c_void_p, c_int]),
     "bpm_headmap_upload": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p,
                                    POINTER(c_int32)]),
     "bpm_batch_create": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), POINTER(c_void_p)]),

@@ -141,6 +141,26 @@ class Context:
                                             byref(mid)))
         return mid.value
 
+    def head_field(self, geometry, nx: int, ny: int, nz: int, h_nm: float, origin_nm, out=None):
+        """Field of a saturated main pole on a voxel grid (bpm_head_field_solve).  geometry: a
+        mapping with the bpm_pole_geometry field names.  Returns a synth.HeadMap (host), or fills
+        the torch device tensor `out` ([nz][ny][nx][3] float32) and returns it."""
+        from . import synth
+        g = L.bpm_pole_geometry()
+        for f, _ in L.bpm_pole_geometry._fields_:
+            if f != "reserved":
+                setattr(g, f, type(getattr(g, f))(geometry[f]))
+        org = np.ascontiguousarray(origin_nm, np.float32)
+        if out is not None:
+            with self.device_order():
+                L.check(self.lib.bpm_head_field_solve(self.h, byref(g), int(nx), int(ny), int(nz), float(h_nm),
+                                                      L.ptr(org), L.ptr(out), 1))
+            return out
+        B = np.zeros((nz, ny, nx, 3), np.float32)
+        L.check(self.lib.bpm_head_field_solve(self.h, byref(g), int(nx), int(ny), int(nz), float(h_nm), L.ptr(org),
+                                              L.ptr(B), 0))
+        return synth.HeadMap(B_T=B, origin_nm=org.copy(), h_nm=float(h_nm), info=dict(geometry))
+
     # ---- batches
     def batch(self, islands, params, precision=L.PREC_BF16X3, map_id=-1) -> "Batch":
         return Batch(self, islands, params, precision, map_id)

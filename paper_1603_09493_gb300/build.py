@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libbpmllg.so")
 
 SOURCES = ["bpm_api.cu", "bpm_assemble.cu", "bpm_step.cu", "bpm_gemm_simt.cu", "bpm_gemm_tc.cu",
            "bpm_noalloc.cu", "bpm_mlp.cu", "bpm_plain.cu",
-           "bpm_gemm_grouped.cu", "bpm_gemm_pair.cu", "bpm_neb.cu", "bpm_gp.cu"]
+           "bpm_gemm_grouped.cu", "bpm_gemm_pair.cu", "bpm_neb.cu", "bpm_gp.cu", "bpm_head.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

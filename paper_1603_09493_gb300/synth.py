@@ -294,6 +294,19 @@ def synthetic_head_map(nx=64, ny=64, nz=16, h_nm=1.0, B_peak_T=1.3, tilt_deg=25.
                              decay_nm=decay_nm, d_ref_nm=d_ref_nm))
 
 
+def pole_geometry(**overrides) -> dict:
+    """Main-pole geometry for the head-field solve (field names of bpm_pole_geometry): Table I's
+    initial design (pole tip width 14 nm, trailing edge angle 20 deg, side edge angle 15 deg,
+    taper 75 deg), the yoke edge 153 nm above the ABS, CoFe at 2.4 T (Table II), a 20 nm deep
+    ABS footprint, and the frame of synthetic_head_map: island tops at z = 10 nm, the ABS 6 nm
+    above them (the paper's head-media spacing), the soft under-layer 20 nm below the ABS."""
+    g = dict(pole_tip_width_nm=14.0, trailing_edge_angle_deg=20.0, side_edge_angle_deg=15.0,
+             taper_angle_deg=75.0, abs_thickness_nm=20.0, yoke_edge_nm=153.0, Js_T=2.4,
+             z_abs_nm=16.0, z_sul_nm=-4.0, sul_image=1)
+    g.update(overrides)
+    return g
+
+
 # --------------------------------------------------------------------------
 # run parameters and workload presets
 # --------------------------------------------------------------------------

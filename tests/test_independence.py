@@ -72,8 +72,8 @@ def _functions_importing_the_oracle(path):
 def test_bench_and_smoke_reach_the_oracle_only_from_their_baseline_legs():
     bench = _functions_importing_the_oracle(os.path.join(ROOT, "bench.py"))
     # the worker-pool functions and oracle_step_count serve cpu_baseline and the reference arm
-    # (main_reference); measure_neb / measure_ego time their own oracle baselines
+    # (main_reference); measure_neb / measure_ego / measure_head_field time their own oracle baselines
     assert bench <= {"cpu_baseline", "_oracle_worker_init", "_oracle_worker_run", "oracle_step_count",
-                     "measure_neb", "measure_ego", "main_reference"}, bench
+                     "measure_neb", "measure_ego", "measure_head_field", "main_reference"}, bench
     entry = _functions_importing_the_oracle(os.path.join(ROOT, "__graft_entry__.py"))
     assert entry <= {"smoke", "_smoke_surrogate"}, entry
