@@ -313,8 +313,8 @@ enum { BPM_RASTER_AUTO = 0, BPM_RASTER_M = 1, BPM_RASTER_N = 2 };
 
 /* Launch configuration of a batch's kernels.  A new batch starts with
  * gemm_tile_n 256, stage_threads 256, gemm_raster AUTO, stage_islands 2,
- * gemm_k_block 32 and gemm_pair 0 (the fastest on the census and uneven
- * batches measured). */
+ * gemm_k_block 32, gemm_pair 0 and streams 2 (the fastest on the census and
+ * uneven batches measured). */
 typedef struct {
     int32_t gemm_tile_n;     /* output columns per demag-GEMM CTA: 256 or 128 */
     int32_t stage_threads;   /* threads per Heun-stage CTA: 128, 256 or 512 */
@@ -324,14 +324,20 @@ typedef struct {
     int32_t gemm_pair;       /* 1: 256 x 256 GEMM tiles on the two SMs of a CTA pair (tcgen05
                                 cta_group::2; needs gemm_tile_n 256), 0: 128 x gemm_tile_n tiles
                                 on one SM */
+    int32_t streams;         /* 2: the interval graph integrates two halves of the batch (split at
+                                a multiple of 128 islands) as two chains on two streams, so that
+                                one half's GEMM overlaps the other half's stage kernels; 1 (0 = 1):
+                                one chain.  2 applies to a one-mesh batch of at least 256 islands
+                                at a tensor-core precision and acts as 1 otherwise.  The states are
+                                bitwise the same either way. */
     double  gemm_ms;         /* measured time of one demag GEMM over the batch (autotune output) */
     double  stage_ms;        /* measured time of one predictor + one corrector over the batch */
 } bpm_tuning;
 
 /* Autotuner: time every (gemm_tile_n, gemm_raster, gemm_k_block, gemm_pair) candidate of the demag GEMM
  * and every (stage_threads, stage_islands) candidate on this batch with CUDA events (reps Heun
- * steps each, kernel by kernel), apply the fastest of each, and report them in
- * *chosen (nullable).  The
+ * steps each, kernel by kernel), apply the fastest of each, then time reps whole intervals with
+ * streams 1 and 2 where 2 applies, and report the choice in *chosen (nullable).  The
  * state advances by the timed steps but the batch clock does not; call
  * bpm_batch_set_state afterwards to restart a run.  Tile shapes are an
  * implementation choice of this library, not of the paper. */

@@ -77,7 +77,7 @@ class bpm_pole_geometry(ctypes.Structure):
 
 class bpm_tuning(ctypes.Structure):
     _fields_ = [("gemm_tile_n", c_int32), ("stage_threads", c_int32), ("gemm_raster", c_int32), ("stage_islands", c_int32),
-                ("gemm_k_block", c_int32), ("gemm_pair", c_int32),
+                ("gemm_k_block", c_int32), ("gemm_pair", c_int32), ("streams", c_int32),
                 ("gemm_ms", c_double), ("stage_ms", c_double)]
 
 

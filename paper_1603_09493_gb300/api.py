@@ -431,12 +431,12 @@ class Batch:
         L.check(self.lib.bpm_batch_autotune(self.h, int(reps), byref(t)))
         return dict(gemm_tile_n=t.gemm_tile_n, stage_threads=t.stage_threads, gemm_raster=t.gemm_raster,
                     stage_islands=t.stage_islands, gemm_k_block=t.gemm_k_block, gemm_pair=t.gemm_pair,
-                    gemm_ms=t.gemm_ms, stage_ms=t.stage_ms)
+                    streams=t.streams, gemm_ms=t.gemm_ms, stage_ms=t.stage_ms)
 
     def set_tuning(self, gemm_tile_n: int, stage_threads: int, gemm_raster: int = L.RASTER_AUTO,
-                   stage_islands: int = 1, gemm_k_block: int = 32, gemm_pair: int = 0, **_):
+                   stage_islands: int = 1, gemm_k_block: int = 32, gemm_pair: int = 0, streams: int = 2, **_):
         t = L.bpm_tuning(int(gemm_tile_n), int(stage_threads), int(gemm_raster), int(stage_islands),
-                         int(gemm_k_block), int(gemm_pair), 0.0, 0.0)
+                         int(gemm_k_block), int(gemm_pair), int(streams), 0.0, 0.0)
         L.check(self.lib.bpm_batch_set_tuning(self.h, byref(t)))
 
     def tuning_key(self, device_name: str = "") -> str:

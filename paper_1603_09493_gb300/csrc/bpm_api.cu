@@ -139,6 +139,14 @@ struct bpm_batch {
     int k_block = 32;                 // demag GEMM K depth per pipeline stage
     int pair = 0;                     // demag GEMM on CTA pairs (256 x 256 tiles)
     GroupedGemm gg;                   // tensor-core demag GEMM over all groups (BF16 precisions)
+    // two-stream intervals (tuning streams = 2): islands [0, split) and [split, B) of the one
+    // group run as two chains, the second on side2; split = 0 when the mode is off
+    int streams = 2;
+    int split = 0;
+    GroupedGemm gg_half[2];
+    StepArgs half[2]{};
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t fork_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -177,6 +185,60 @@ int setup_grouped_gemm(bpm_batch* bt) {
     }
     return grouped_gemm_setup(&bt->gg, ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1, bt->raster,
                               bt->k_block, bt->ctx->l2_bytes, bt->pair);
+}
+
+// The two halves of a two-stream batch: rows [0, split) and [split, Bp) of the one group, split a
+// multiple of 128 islands (the GEMM's M tile), each with its own GEMM over its operand rows and
+// its own view of the stage arguments.  split stays 0 where the mode does not apply.
+int setup_halves(bpm_batch* bt) {
+    for (auto& h : bt->gg_half) grouped_gemm_free(&h);
+    bt->split = 0;
+    if (bt->streams != 2 || !tensor_core_precision(bt) || bt->groups.size() != 1) return BPM_OK;
+    Group& g = bt->groups[0];
+    const int split = kIslandPad * ((g.B + 2 * kIslandPad - 1) / (2 * kIslandPad));
+    if (g.B < 2 * kIslandPad || split >= g.B) return BPM_OK;
+    if (!bt->side2) {
+        if (cudaStreamCreateWithFlags(&bt->side2, cudaStreamNonBlocking) != cudaSuccess) {
+            set_error("stream creation failed");
+            return BPM_ERR_CUDA;
+        }
+        for (auto& e : bt->fork_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                set_error("event creation failed");
+                return BPM_ERR_CUDA;
+            }
+    }
+    const int K = g.mesh->K();
+    const size_t off = (size_t)split * K, S = (size_t)split * 3 * g.mesh->n_pad;
+    const int rows[2] = {split, g.Bp - split};
+    for (int h = 0; h < 2; ++h) {
+        const size_t o = h ? off : 0;
+        std::vector<GemmOperands> ops{GemmOperands{g.Ahi + o, g.Alo + o, g.mesh->Nhi, g.mesh->Nlo, g.Hd + o, rows[h],
+                                                   K, K}};
+        BPM_TRY(grouped_gemm_setup(&bt->gg_half[h], ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1,
+                                   bt->raster, bt->k_block, bt->ctx->l2_bytes, bt->pair));
+        StepArgs a = g.args;
+        if (h) {
+            a.B = g.B - split;
+            a.isl += 3 * (size_t)split;
+            a.m += S;
+            a.ms += S;
+            a.k1 += S;
+            a.Hd += off;
+            if (a.A32) a.A32 += off;
+            if (a.Ahi) a.Ahi += off;
+            if (a.Alo) a.Alo += off;
+            a.mz_prev += split;
+            a.t_sw += split;
+            a.crossed += split;
+            a.status += split;
+        } else {
+            a.B = split;
+        }
+        bt->half[h] = a;
+    }
+    bt->split = split;
+    return BPM_OK;
 }
 
 // demag GEMM of every group's current operand A -> Hd: one persistent launch
@@ -274,7 +336,24 @@ void launch_stage_all(bpm_batch* bt, const StageLaunches& L, int stage, int j, c
 // one output interval of every group; groups of a multi-mesh batch are forked
 // over side streams so that their kernels can run concurrently
 int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
-    if (tensor_core_precision(bt)) {
+    if (bt->split > 0) {
+        // two chains: the first half on s, the second on side2 (forked from and joined into s);
+        // each chain runs the Heun steps of its own islands in order, so one half's GEMM can run
+        // while the other half's stage kernels do
+        BPM_CK(cudaEventRecord(bt->fork_ev[0], s));
+        BPM_CK(cudaStreamWaitEvent(bt->side2, bt->fork_ev[0], 0));
+        for (int h = 0; h < 2; ++h) {
+            cudaStream_t sh = h ? bt->side2 : s;
+            for (int j = 0; j < bt->p.substeps; ++j) {
+                BPM_TRY(grouped_gemm_launch(sh, bt->gg_half[h], bt->ctx->sm_count, bt->gemm_err));
+                launch_stage1(bt->half[h], j, sh);
+                BPM_TRY(grouped_gemm_launch(sh, bt->gg_half[h], bt->ctx->sm_count, bt->gemm_err));
+                launch_stage2(bt->half[h], j, sh);
+            }
+        }
+        BPM_CK(cudaEventRecord(bt->fork_ev[1], bt->side2));
+        BPM_CK(cudaStreamWaitEvent(s, bt->fork_ev[1], 0));
+    } else if (tensor_core_precision(bt)) {
         // one grouped GEMM launch and one stage launch per class per Heun stage
         StageLaunches L;
         if (bt->groups.size() > 1) BPM_TRY(build_stage_launches(bt, &L));
@@ -324,6 +403,10 @@ void free_batch(bpm_batch* bt) {
     if (bt->graph) cudaGraphDestroy(bt->graph);
     for (auto& g : bt->groups) free_group(g);
     grouped_gemm_free(&bt->gg);
+    for (auto& h : bt->gg_half) grouped_gemm_free(&h);
+    if (bt->side2) cudaStreamDestroy(bt->side2);
+    for (auto e : bt->fork_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(bt->gemm_err);
     cudaFree(bt->interval);
     for (auto s : bt->side) cudaStreamDestroy(s);
@@ -343,6 +426,56 @@ int dalloc(T** p, size_t count) {
         set_error("cudaMemset failed: %s", cudaGetErrorString(e));
         return BPM_ERR_CUDA;
     }
+    return BPM_OK;
+}
+
+// the batch's interval graph, captured on first use
+int ensure_graph(bpm_batch* bt) {
+    if (bt->exec) return BPM_OK;
+    cudaStream_t s = bt->ctx->stream;
+    BPM_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int r = enqueue_interval(bt, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (r != BPM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess) {
+        set_error("graph capture failed: %s", cudaGetErrorString(e));
+        return BPM_ERR_CUDA;
+    }
+    bt->graph = g;
+    BPM_CK(cudaGraphInstantiate(&bt->exec, g, 0));
+    return BPM_OK;
+}
+
+// average time (ms, CUDA events) of `reps` launches of the interval graph; the state advances,
+// the batch clock (the device interval counter) is put back
+int time_intervals(bpm_batch* bt, int reps, double* ms) {
+    BPM_TRY(ensure_graph(bt));
+    cudaStream_t s = bt->ctx->stream;
+    long long it0 = 0;
+    BPM_CK(cudaMemcpyAsync(&it0, bt->interval, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    BPM_CK(cudaStreamSynchronize(s));
+    cudaEvent_t e0, e1;
+    BPM_CK(cudaEventCreate(&e0));
+    BPM_CK(cudaEventCreate(&e1));
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps; ++i) cudaGraphLaunch(bt->exec, s);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bt->interval, &it0, sizeof(long long), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error("interval timing: %s", cudaGetErrorString(e));
+        return BPM_ERR_CUDA;
+    }
+    *ms = t / reps;
     return BPM_OK;
 }
 
@@ -743,6 +876,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         if (r != BPM_OK) set_error("stream/event creation failed");
     }
     if (r == BPM_OK && tensor_core_precision(bt)) r = setup_grouped_gemm(bt);
+    if (r == BPM_OK) r = setup_halves(bt);
     if (r != BPM_OK) {
         free_batch(bt);
         return r;
@@ -837,22 +971,7 @@ int bpm_batch_advance(bpm_batch* bt, int32_t n_intervals) {
     }
     BPM_TRY(ensure_device(bt->ctx));
     cudaStream_t s = bt->ctx->stream;
-    if (!bt->exec && n_intervals > 0) {
-        BPM_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        int r = enqueue_interval(bt, s);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(s, &g);
-        if (r != BPM_OK) {
-            if (g) cudaGraphDestroy(g);
-            return r;
-        }
-        if (e != cudaSuccess) {
-            set_error("graph capture failed: %s", cudaGetErrorString(e));
-            return BPM_ERR_CUDA;
-        }
-        bt->graph = g;
-        BPM_CK(cudaGraphInstantiate(&bt->exec, g, 0));
-    }
+    if (n_intervals > 0) BPM_TRY(ensure_graph(bt));
     for (int i = 0; i < n_intervals; ++i) BPM_CK(cudaGraphLaunch(bt->exec, s));
     bt->intervals_done += n_intervals;
     return BPM_OK;
@@ -1096,10 +1215,10 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
         (t->gemm_raster != BPM_RASTER_AUTO && t->gemm_raster != BPM_RASTER_M && t->gemm_raster != BPM_RASTER_N) ||
         t->stage_islands < 0 || t->stage_islands > 2 || (t->stage_islands == 2 && t->stage_threads != 256) ||
         (t->gemm_k_block != 0 && t->gemm_k_block != 32 && t->gemm_k_block != 64) || t->gemm_pair < 0 ||
-        t->gemm_pair > 1 || (t->gemm_pair == 1 && t->gemm_tile_n != 256)) {
+        t->gemm_pair > 1 || (t->gemm_pair == 1 && t->gemm_tile_n != 256) || t->streams < 0 || t->streams > 2) {
         set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512, gemm_raster 0|1|2, "
                   "stage_islands 0|1|2 with 2 only at 256 threads, gemm_k_block 0|32|64, gemm_pair 0|1 with 1 "
-                  "only at gemm_tile_n 256)");
+                  "only at gemm_tile_n 256, streams 0|1|2)");
         return BPM_ERR_ARG;
     }
     BPM_TRY(ensure_device(bt->ctx));
@@ -1108,12 +1227,15 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
     bt->raster = t->gemm_raster;
     bt->k_block = t->gemm_k_block == 64 ? 64 : 32;
     bt->pair = t->gemm_pair;
+    bt->streams = t->streams == 2 ? 2 : 1;
     for (auto& g : bt->groups) {
         g.args.threads = t->stage_threads;
         g.args.ipb = t->stage_islands == 2 ? 2 : 1;
     }
     drop_graph(bt);   // the graph holds the old launch configurations
     if (tensor_core_precision(bt)) BPM_TRY(setup_grouped_gemm(bt));
+    BPM_TRY(setup_halves(bt));
+    for (auto& h : bt->gg_half) h.wait_ns = bt->gg.wait_ns;
     return BPM_OK;
 }
 
@@ -1135,7 +1257,7 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
     for (int ti = 0; ti < (tc ? 3 : 1); ++ti)
         for (int ri = 0; ri < (tc ? 3 : 1); ++ri)
             for (int ki = 0; ki < (tc ? 2 : 1); ++ki) {
-                bpm_tuning t{tiles[ti], 256, rasters[ri], 1, kblocks[ki], pairs[ti], 0, 0};
+                bpm_tuning t{tiles[ti], 256, rasters[ri], 1, kblocks[ki], pairs[ti], 1, 0, 0};
                 BPM_TRY(bpm_batch_set_tuning(bt, &t));
                 double g = 0, s1 = 0, s2 = 0;
                 BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));   // warm-up
@@ -1152,7 +1274,7 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
     int bt_i = 1;
     for (int hi = 0; hi < 4; ++hi) {
         const int nt = hi < 3 ? threads[hi] : 256, ipb = hi < 3 ? 1 : 2;
-        bpm_tuning t{bt_n, nt, bt_r, ipb, bt_k, bt_p, 0, 0};
+        bpm_tuning t{bt_n, nt, bt_r, ipb, bt_k, bt_p, 1, 0, 0};
         BPM_TRY(bpm_batch_set_tuning(bt, &t));
         double g = 0, s1 = 0, s2 = 0;
         BPM_TRY(bpm_batch_kernel_times(bt, 1, &g, &s1, &s2));
@@ -1163,7 +1285,23 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
             bt_i = ipb;
         }
     }
-    bpm_tuning t{bt_n, bt_t, bt_r, bt_i, bt_k, bt_p, best_g, best_s};
+    // one chain or two: whole intervals of the interval graph, where two chains apply
+    int bt_s = 1;
+    if (tensor_core_precision(bt) && bt->groups.size() == 1 && bt->groups[0].B >= 2 * kIslandPad) {
+        double best_i = 1e300;
+        for (int ns = 1; ns <= 2; ++ns) {
+            bpm_tuning t{bt_n, bt_t, bt_r, bt_i, bt_k, bt_p, ns, 0, 0};
+            BPM_TRY(bpm_batch_set_tuning(bt, &t));
+            double ms = 0;
+            BPM_TRY(time_intervals(bt, 1, &ms));   // capture and warm-up
+            BPM_TRY(time_intervals(bt, reps, &ms));
+            if (ms < best_i) {
+                best_i = ms;
+                bt_s = ns;
+            }
+        }
+    }
+    bpm_tuning t{bt_n, bt_t, bt_r, bt_i, bt_k, bt_p, bt_s, best_g, best_s};
     BPM_TRY(bpm_batch_set_tuning(bt, &t));
     if (chosen) *chosen = t;
     return BPM_OK;
@@ -1188,6 +1326,7 @@ int bpm_debug_set_gemm_wait(bpm_batch* bt, double wait_ns) {
     BPM_TRY(ensure_device(bt->ctx));
     BPM_CK(cudaStreamSynchronize(bt->ctx->stream));
     bt->gg.wait_ns = (unsigned long long)wait_ns;
+    for (auto& h : bt->gg_half) h.wait_ns = bt->gg.wait_ns;
     drop_graph(bt);   // the graph holds the old kernel arguments
     return BPM_OK;
 }

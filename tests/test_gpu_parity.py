@@ -239,6 +239,46 @@ def test_autotuner_choices_do_not_change_results(ctx, small, headmap):
         assert np.array_equal(bt.read()["m"], outs[0]["m"])
 
 
+def test_two_stream_intervals_give_the_same_states(ctx, small, headmap):
+    # tuning streams = 2 integrates the islands below and above a split (a multiple of 128) as two
+    # chains on two streams; every island sees the same kernels, so m, the switch data and <m_z>
+    # are bitwise those of one chain.  300 islands split 256 + 44 (a ragged second half), 512
+    # split 256 + 256; 255 islands are too few and run as one chain.  A real GEMM wait that runs
+    # out inside the two-chain graph reports BPM_ERR_TIMEOUT like the one-chain graph.
+    mesh, mats, ops, mid = small
+    hm, hid = headmap
+    p = synth.RunParams(dt_ps=0.1, substeps=8, alpha=0.1, rise_ps=10.0, use_map=True, x0_nm=-3.0,
+                        uniform_T=synth.uniform_field(0.7, 170.0))
+    for B in (300, 512, 255):
+        isl = synth.jittered_islands(B, seed=B, mesh_id=mid)
+        outs = []
+        for streams in (1, 2):
+            with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+                bt.set_tuning(256, 256, L.RASTER_AUTO, 2, 32, streams=streams)
+                bt.advance(30)
+                outs.append(bt.read())
+        for key in ("m", "switched", "t_sw", "mz", "status"):
+            assert np.array_equal(outs[1][key], outs[0][key]), (B, key)
+        assert np.all(outs[1]["status"] == 0)
+    isl = synth.jittered_islands(300, seed=5, mesh_id=mid)
+    with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+        bt.set_tuning(256, 256, L.RASTER_AUTO, 2, 32, streams=2)
+        L.check(ctx.lib.bpm_debug_set_gemm_wait(bt.h, 1000.0))        # 1 us
+        bt.advance(2)
+        with pytest.raises(L.BpmError) as e:
+            bt.read()
+        assert e.value.code == L.BPM_ERR_TIMEOUT
+        L.check(ctx.lib.bpm_debug_set_gemm_wait(bt.h, 0.0))
+        L.check(ctx.lib.bpm_debug_set_gemm_error(bt.h, 0))
+        bt.set_state(None, 0.0)
+        bt.advance(2)
+        assert np.all(bt.read()["status"] == 0)
+    with ctx.batch(synth.jittered_islands(512, seed=7, mesh_id=mid), p, precision=L.PREC_BF16X3,
+                   map_id=hid) as bt:
+        t = bt.autotune(reps=2)
+        assert t["streams"] in (1, 2)
+
+
 def test_two_islands_per_cta_odd_groups(ctx, small, headmap):
     # two islands per stage CTA over two mesh groups of odd sizes (the last CTA
     # of each group holds one island): the same m and switch data as one island
