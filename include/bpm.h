@@ -324,12 +324,12 @@ typedef struct {
     int32_t gemm_pair;       /* 1: 256 x 256 GEMM tiles on the two SMs of a CTA pair (tcgen05
                                 cta_group::2; needs gemm_tile_n 256), 0: 128 x gemm_tile_n tiles
                                 on one SM */
-    int32_t streams;         /* 2: the interval graph integrates two halves of the batch (split at
-                                a multiple of 128 islands) as two chains on two streams, so that
-                                one half's GEMM overlaps the other half's stage kernels; 1 (0 = 1):
-                                one chain.  2 applies to a one-mesh batch of at least 256 islands
-                                at a tensor-core precision and acts as 1 otherwise.  The states are
-                                bitwise the same either way. */
+    int32_t streams;         /* 2 .. 4: the interval graph integrates the batch as that many chunks
+                                of islands (a multiple of 128 each, the last takes the rest), each a
+                                chain on its own stream, so that one chain's GEMM overlaps another
+                                chain's stage kernels; 1 (0 = 1): one chain.  Applies to a one-mesh
+                                batch at a tensor-core precision with at least two chunks, and acts
+                                as 1 otherwise.  The states are bitwise the same either way. */
     double  gemm_ms;         /* measured time of one demag GEMM over the batch (autotune output) */
     double  stage_ms;        /* measured time of one predictor + one corrector over the batch */
 } bpm_tuning;
@@ -337,7 +337,7 @@ typedef struct {
 /* Autotuner: time every (gemm_tile_n, gemm_raster, gemm_k_block, gemm_pair) candidate of the demag GEMM
  * and every (stage_threads, stage_islands) candidate on this batch with CUDA events (reps Heun
  * steps each, kernel by kernel), apply the fastest of each, then time reps whole intervals with
- * streams 1 and 2 where 2 applies, and report the choice in *chosen (nullable).  The
+ * streams 1 .. 4 where several chains apply, and report the choice in *chosen (nullable).  The
  * state advances by the timed steps but the batch clock does not; call
  * bpm_batch_set_state afterwards to restart a run.  Tile shapes are an
  * implementation choice of this library, not of the paper. */

@@ -139,14 +139,15 @@ struct bpm_batch {
     int k_block = 32;                 // demag GEMM K depth per pipeline stage
     int pair = 0;                     // demag GEMM on CTA pairs (256 x 256 tiles)
     GroupedGemm gg;                   // tensor-core demag GEMM over all groups (BF16 precisions)
-    // two-stream intervals (tuning streams = 2): islands [0, split) and [split, B) of the one
-    // group run as two chains, the second on side2; split = 0 when the mode is off
+    // multi-stream intervals (tuning streams = 2 .. 4): consecutive chunks of `chunk` islands
+    // (the last one shorter) of the one group run as `chains` chains, chain c > 0 on
+    // chain_stream[c - 1]; chains = 0 when the mode is off
     int streams = 2;
-    int split = 0;
-    GroupedGemm gg_half[2];
-    StepArgs half[2]{};
-    cudaStream_t side2 = nullptr;
-    cudaEvent_t fork_ev[2] = {nullptr, nullptr};
+    int chains = 0, chunk = 0;
+    GroupedGemm gg_chain[kMaxChains];
+    StepArgs chain_args[kMaxChains]{};
+    cudaStream_t chain_stream[kMaxChains - 1] = {};
+    cudaEvent_t chain_ev[kMaxChains] = {};
 };
 
 namespace {
@@ -187,57 +188,56 @@ int setup_grouped_gemm(bpm_batch* bt) {
                               bt->k_block, bt->ctx->l2_bytes, bt->pair);
 }
 
-// The two halves of a two-stream batch: rows [0, split) and [split, Bp) of the one group, split a
-// multiple of 128 islands (the GEMM's M tile), each with its own GEMM over its operand rows and
-// its own view of the stage arguments.  split stays 0 where the mode does not apply.
-int setup_halves(bpm_batch* bt) {
-    for (auto& h : bt->gg_half) grouped_gemm_free(&h);
-    bt->split = 0;
-    if (bt->streams != 2 || !tensor_core_precision(bt) || bt->groups.size() != 1) return BPM_OK;
+// The chains of a multi-stream batch: the one group's islands cut into `streams` chunks of a
+// multiple of 128 islands (the GEMM's M tile; the last chunk takes the rest), each with its own
+// GEMM over its operand rows and its own view of the stage arguments.  chains stays 0 where the
+// mode does not apply (another precision, several meshes, fewer than two chunks).
+int setup_chains(bpm_batch* bt) {
+    for (auto& h : bt->gg_chain) grouped_gemm_free(&h);
+    bt->chains = 0;
+    if (bt->streams < 2 || !tensor_core_precision(bt) || bt->groups.size() != 1) return BPM_OK;
     Group& g = bt->groups[0];
-    const int split = kIslandPad * ((g.B + 2 * kIslandPad - 1) / (2 * kIslandPad));
-    if (g.B < 2 * kIslandPad || split >= g.B) return BPM_OK;
-    if (!bt->side2) {
-        if (cudaStreamCreateWithFlags(&bt->side2, cudaStreamNonBlocking) != cudaSuccess) {
+    const int chunk = kIslandPad * ((g.B + bt->streams * kIslandPad - 1) / (bt->streams * kIslandPad));
+    const int chains = (g.B + chunk - 1) / chunk;
+    if (chains < 2) return BPM_OK;
+    for (int c = 0; c < kMaxChains - 1; ++c)
+        if (!bt->chain_stream[c] && cudaStreamCreateWithFlags(&bt->chain_stream[c], cudaStreamNonBlocking) !=
+                                        cudaSuccess) {
             set_error("stream creation failed");
             return BPM_ERR_CUDA;
         }
-        for (auto& e : bt->fork_ev)
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-                set_error("event creation failed");
-                return BPM_ERR_CUDA;
-            }
-    }
+    for (auto& e : bt->chain_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            set_error("event creation failed");
+            return BPM_ERR_CUDA;
+        }
     const int K = g.mesh->K();
-    const size_t off = (size_t)split * K, S = (size_t)split * 3 * g.mesh->n_pad;
-    const int rows[2] = {split, g.Bp - split};
-    for (int h = 0; h < 2; ++h) {
-        const size_t o = h ? off : 0;
-        std::vector<GemmOperands> ops{GemmOperands{g.Ahi + o, g.Alo + o, g.mesh->Nhi, g.mesh->Nlo, g.Hd + o, rows[h],
-                                                   K, K}};
-        BPM_TRY(grouped_gemm_setup(&bt->gg_half[h], ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1,
+    for (int c = 0; c < chains; ++c) {
+        const int b0 = c * chunk;
+        const int rows = c + 1 < chains ? chunk : g.Bp - b0;   // the last chunk's GEMM covers the padding
+        const size_t off = (size_t)b0 * K, S = (size_t)b0 * 3 * g.mesh->n_pad;
+        std::vector<GemmOperands> ops{GemmOperands{g.Ahi + off, g.Alo + off, g.mesh->Nhi, g.mesh->Nlo, g.Hd + off,
+                                                   rows, K, K}};
+        BPM_TRY(grouped_gemm_setup(&bt->gg_chain[c], ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1,
                                    bt->raster, bt->k_block, bt->ctx->l2_bytes, bt->pair));
         StepArgs a = g.args;
-        if (h) {
-            a.B = g.B - split;
-            a.isl += 3 * (size_t)split;
-            a.m += S;
-            a.ms += S;
-            a.k1 += S;
-            a.Hd += off;
-            if (a.A32) a.A32 += off;
-            if (a.Ahi) a.Ahi += off;
-            if (a.Alo) a.Alo += off;
-            a.mz_prev += split;
-            a.t_sw += split;
-            a.crossed += split;
-            a.status += split;
-        } else {
-            a.B = split;
-        }
-        bt->half[h] = a;
+        a.B = std::min(chunk, g.B - b0);
+        a.isl += 3 * (size_t)b0;
+        a.m += S;
+        a.ms += S;
+        a.k1 += S;
+        a.Hd += off;
+        if (a.A32) a.A32 += off;
+        if (a.Ahi) a.Ahi += off;
+        if (a.Alo) a.Alo += off;
+        a.mz_prev += b0;
+        a.t_sw += b0;
+        a.crossed += b0;
+        a.status += b0;
+        bt->chain_args[c] = a;
     }
-    bt->split = split;
+    bt->chains = chains;
+    bt->chunk = chunk;
     return BPM_OK;
 }
 
@@ -336,23 +336,25 @@ void launch_stage_all(bpm_batch* bt, const StageLaunches& L, int stage, int j, c
 // one output interval of every group; groups of a multi-mesh batch are forked
 // over side streams so that their kernels can run concurrently
 int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
-    if (bt->split > 0) {
-        // two chains: the first half on s, the second on side2 (forked from and joined into s);
-        // each chain runs the Heun steps of its own islands in order, so one half's GEMM can run
-        // while the other half's stage kernels do
-        BPM_CK(cudaEventRecord(bt->fork_ev[0], s));
-        BPM_CK(cudaStreamWaitEvent(bt->side2, bt->fork_ev[0], 0));
-        for (int h = 0; h < 2; ++h) {
-            cudaStream_t sh = h ? bt->side2 : s;
+    if (bt->chains > 0) {
+        // one chain per chunk of islands: chunk 0 on s, chunk c on chain_stream[c - 1] (forked
+        // from and joined into s); each chain runs the Heun steps of its own islands in order, so
+        // one chain's GEMM can run while another chain's stage kernels do
+        BPM_CK(cudaEventRecord(bt->chain_ev[0], s));
+        for (int c = 1; c < bt->chains; ++c) BPM_CK(cudaStreamWaitEvent(bt->chain_stream[c - 1], bt->chain_ev[0], 0));
+        for (int c = 0; c < bt->chains; ++c) {
+            cudaStream_t sc = c ? bt->chain_stream[c - 1] : s;
             for (int j = 0; j < bt->p.substeps; ++j) {
-                BPM_TRY(grouped_gemm_launch(sh, bt->gg_half[h], bt->ctx->sm_count, bt->gemm_err));
-                launch_stage1(bt->half[h], j, sh);
-                BPM_TRY(grouped_gemm_launch(sh, bt->gg_half[h], bt->ctx->sm_count, bt->gemm_err));
-                launch_stage2(bt->half[h], j, sh);
+                BPM_TRY(grouped_gemm_launch(sc, bt->gg_chain[c], bt->ctx->sm_count, bt->gemm_err));
+                launch_stage1(bt->chain_args[c], j, sc);
+                BPM_TRY(grouped_gemm_launch(sc, bt->gg_chain[c], bt->ctx->sm_count, bt->gemm_err));
+                launch_stage2(bt->chain_args[c], j, sc);
             }
         }
-        BPM_CK(cudaEventRecord(bt->fork_ev[1], bt->side2));
-        BPM_CK(cudaStreamWaitEvent(s, bt->fork_ev[1], 0));
+        for (int c = 1; c < bt->chains; ++c) {
+            BPM_CK(cudaEventRecord(bt->chain_ev[c], bt->chain_stream[c - 1]));
+            BPM_CK(cudaStreamWaitEvent(s, bt->chain_ev[c], 0));
+        }
     } else if (tensor_core_precision(bt)) {
         // one grouped GEMM launch and one stage launch per class per Heun stage
         StageLaunches L;
@@ -403,9 +405,10 @@ void free_batch(bpm_batch* bt) {
     if (bt->graph) cudaGraphDestroy(bt->graph);
     for (auto& g : bt->groups) free_group(g);
     grouped_gemm_free(&bt->gg);
-    for (auto& h : bt->gg_half) grouped_gemm_free(&h);
-    if (bt->side2) cudaStreamDestroy(bt->side2);
-    for (auto e : bt->fork_ev)
+    for (auto& h : bt->gg_chain) grouped_gemm_free(&h);
+    for (auto st : bt->chain_stream)
+        if (st) cudaStreamDestroy(st);
+    for (auto e : bt->chain_ev)
         if (e) cudaEventDestroy(e);
     cudaFree(bt->gemm_err);
     cudaFree(bt->interval);
@@ -876,7 +879,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         if (r != BPM_OK) set_error("stream/event creation failed");
     }
     if (r == BPM_OK && tensor_core_precision(bt)) r = setup_grouped_gemm(bt);
-    if (r == BPM_OK) r = setup_halves(bt);
+    if (r == BPM_OK) r = setup_chains(bt);
     if (r != BPM_OK) {
         free_batch(bt);
         return r;
@@ -1215,10 +1218,11 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
         (t->gemm_raster != BPM_RASTER_AUTO && t->gemm_raster != BPM_RASTER_M && t->gemm_raster != BPM_RASTER_N) ||
         t->stage_islands < 0 || t->stage_islands > 2 || (t->stage_islands == 2 && t->stage_threads != 256) ||
         (t->gemm_k_block != 0 && t->gemm_k_block != 32 && t->gemm_k_block != 64) || t->gemm_pair < 0 ||
-        t->gemm_pair > 1 || (t->gemm_pair == 1 && t->gemm_tile_n != 256) || t->streams < 0 || t->streams > 2) {
+        t->gemm_pair > 1 || (t->gemm_pair == 1 && t->gemm_tile_n != 256) || t->streams < 0 ||
+        t->streams > kMaxChains) {
         set_error("bad tuning (gemm_tile_n 128|256, stage_threads 128|256|512, gemm_raster 0|1|2, "
                   "stage_islands 0|1|2 with 2 only at 256 threads, gemm_k_block 0|32|64, gemm_pair 0|1 with 1 "
-                  "only at gemm_tile_n 256, streams 0|1|2)");
+                  "only at gemm_tile_n 256, streams 0 .. 4)");
         return BPM_ERR_ARG;
     }
     BPM_TRY(ensure_device(bt->ctx));
@@ -1227,15 +1231,15 @@ int bpm_batch_set_tuning(bpm_batch* bt, const bpm_tuning* t) {
     bt->raster = t->gemm_raster;
     bt->k_block = t->gemm_k_block == 64 ? 64 : 32;
     bt->pair = t->gemm_pair;
-    bt->streams = t->streams == 2 ? 2 : 1;
+    bt->streams = std::max(1, (int)t->streams);
     for (auto& g : bt->groups) {
         g.args.threads = t->stage_threads;
         g.args.ipb = t->stage_islands == 2 ? 2 : 1;
     }
     drop_graph(bt);   // the graph holds the old launch configurations
     if (tensor_core_precision(bt)) BPM_TRY(setup_grouped_gemm(bt));
-    BPM_TRY(setup_halves(bt));
-    for (auto& h : bt->gg_half) h.wait_ns = bt->gg.wait_ns;
+    BPM_TRY(setup_chains(bt));
+    for (auto& h : bt->gg_chain) h.wait_ns = bt->gg.wait_ns;
     return BPM_OK;
 }
 
@@ -1285,11 +1289,11 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
             bt_i = ipb;
         }
     }
-    // one chain or two: whole intervals of the interval graph, where two chains apply
+    // one chain or several: whole intervals of the interval graph, where several chains apply
     int bt_s = 1;
-    if (tensor_core_precision(bt) && bt->groups.size() == 1 && bt->groups[0].B >= 2 * kIslandPad) {
+    if (tensor_core_precision(bt) && bt->groups.size() == 1 && bt->groups[0].B > kIslandPad) {
         double best_i = 1e300;
-        for (int ns = 1; ns <= 2; ++ns) {
+        for (int ns = 1; ns <= kMaxChains; ++ns) {
             bpm_tuning t{bt_n, bt_t, bt_r, bt_i, bt_k, bt_p, ns, 0, 0};
             BPM_TRY(bpm_batch_set_tuning(bt, &t));
             double ms = 0;
@@ -1326,7 +1330,7 @@ int bpm_debug_set_gemm_wait(bpm_batch* bt, double wait_ns) {
     BPM_TRY(ensure_device(bt->ctx));
     BPM_CK(cudaStreamSynchronize(bt->ctx->stream));
     bt->gg.wait_ns = (unsigned long long)wait_ns;
-    for (auto& h : bt->gg_half) h.wait_ns = bt->gg.wait_ns;
+    for (auto& h : bt->gg_chain) h.wait_ns = bt->gg.wait_ns;
     drop_graph(bt);   // the graph holds the old kernel arguments
     return BPM_OK;
 }

@@ -44,6 +44,9 @@ void set_error(const char* fmt, ...);
 // so that the three components of both islands sit at fixed distances from node j's word.
 constexpr int kIlIslands = 2;
 
+// Chains of islands a batch's interval graph may run on separate streams (tuning streams).
+constexpr int kMaxChains = 4;
+
 // Position (nm) and lumped volume weight V_i / sum V of one node, FP64.
 struct NodeF64 {
     double x, y, z, w;

@@ -240,10 +240,10 @@ def test_autotuner_choices_do_not_change_results(ctx, small, headmap):
 
 
 def test_two_stream_intervals_give_the_same_states(ctx, small, headmap):
-    # tuning streams = 2 integrates the islands below and above a split (a multiple of 128) as two
-    # chains on two streams; every island sees the same kernels, so m, the switch data and <m_z>
-    # are bitwise those of one chain.  300 islands split 256 + 44 (a ragged second half), 512
-    # split 256 + 256; 255 islands are too few and run as one chain.  A real GEMM wait that runs
+    # tuning streams = s integrates chunks of islands (multiples of 128) as chains on their own
+    # streams; every island sees the same kernels, so m, the switch data and <m_z> are bitwise
+    # those of one chain.  300 islands: 256 + 44 (s = 2), 128 + 128 + 44 (s = 3, 4); 512: 256 + 256
+    # (s = 2, 3) or four chunks of 128; 255 islands: 128 + 127.  A real GEMM wait that runs
     # out inside the two-chain graph reports BPM_ERR_TIMEOUT like the one-chain graph.
     mesh, mats, ops, mid = small
     hm, hid = headmap
@@ -252,17 +252,18 @@ def test_two_stream_intervals_give_the_same_states(ctx, small, headmap):
     for B in (300, 512, 255):
         isl = synth.jittered_islands(B, seed=B, mesh_id=mid)
         outs = []
-        for streams in (1, 2):
+        for streams in (1, 2, 3, 4):
             with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
                 bt.set_tuning(256, 256, L.RASTER_AUTO, 2, 32, streams=streams)
                 bt.advance(30)
                 outs.append(bt.read())
-        for key in ("m", "switched", "t_sw", "mz", "status"):
-            assert np.array_equal(outs[1][key], outs[0][key]), (B, key)
-        assert np.all(outs[1]["status"] == 0)
+        for o in outs[1:]:
+            for key in ("m", "switched", "t_sw", "mz", "status"):
+                assert np.array_equal(o[key], outs[0][key]), (B, key)
+            assert np.all(o["status"] == 0)
     isl = synth.jittered_islands(300, seed=5, mesh_id=mid)
     with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
-        bt.set_tuning(256, 256, L.RASTER_AUTO, 2, 32, streams=2)
+        bt.set_tuning(256, 256, L.RASTER_AUTO, 2, 32, streams=3)
         L.check(ctx.lib.bpm_debug_set_gemm_wait(bt.h, 1000.0))        # 1 us
         bt.advance(2)
         with pytest.raises(L.BpmError) as e:
@@ -276,7 +277,7 @@ def test_two_stream_intervals_give_the_same_states(ctx, small, headmap):
     with ctx.batch(synth.jittered_islands(512, seed=7, mesh_id=mid), p, precision=L.PREC_BF16X3,
                    map_id=hid) as bt:
         t = bt.autotune(reps=2)
-        assert t["streams"] in (1, 2)
+        assert t["streams"] in (1, 2, 3, 4)
 
 
 def test_two_islands_per_cta_odd_groups(ctx, small, headmap):
