@@ -313,8 +313,8 @@ enum { BPM_RASTER_AUTO = 0, BPM_RASTER_M = 1, BPM_RASTER_N = 2 };
 
 /* Launch configuration of a batch's kernels.  A new batch starts with
  * gemm_tile_n 256, stage_threads 256, gemm_raster AUTO, stage_islands 2,
- * gemm_k_block 32, gemm_pair 0 and streams 2 (the fastest on the census and
- * uneven batches measured). */
+ * gemm_k_block 32, gemm_pair 0, and streams 2 for a one-mesh batch, 1 for a
+ * multi-mesh batch (the fastest on the census and uneven batches measured). */
 typedef struct {
     int32_t gemm_tile_n;     /* output columns per demag-GEMM CTA: 256 or 128 */
     int32_t stage_threads;   /* threads per Heun-stage CTA: 128, 256 or 512 */
@@ -324,12 +324,13 @@ typedef struct {
     int32_t gemm_pair;       /* 1: 256 x 256 GEMM tiles on the two SMs of a CTA pair (tcgen05
                                 cta_group::2; needs gemm_tile_n 256), 0: 128 x gemm_tile_n tiles
                                 on one SM */
-    int32_t streams;         /* 2 .. 4: the interval graph integrates the batch as that many chunks
-                                of islands (a multiple of 128 each, the last takes the rest), each a
-                                chain on its own stream, so that one chain's GEMM overlaps another
-                                chain's stage kernels; 1 (0 = 1): one chain.  Applies to a one-mesh
-                                batch at a tensor-core precision with at least two chunks, and acts
-                                as 1 otherwise.  The states are bitwise the same either way. */
+    int32_t streams;         /* 2 .. 4: the interval graph integrates the batch as up to that many
+                                chains, each on its own stream, so that one chain's GEMM overlaps
+                                another chain's stage kernels: a one-mesh batch cut into chunks of
+                                islands (a multiple of 128 each, the last takes the rest), a
+                                multi-mesh batch's groups dealt to chains of about equal GEMM work.
+                                1 (0 = 1): one chain.  Applies at the tensor-core precisions and
+                                acts as 1 otherwise.  The states are bitwise the same either way. */
     double  gemm_ms;         /* measured time of one demag GEMM over the batch (autotune output) */
     double  stage_ms;        /* measured time of one predictor + one corrector over the batch */
 } bpm_tuning;

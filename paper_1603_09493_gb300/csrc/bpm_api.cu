@@ -145,7 +145,8 @@ struct bpm_batch {
     int streams = 2;
     int chains = 0, chunk = 0;
     GroupedGemm gg_chain[kMaxChains];
-    StepArgs chain_args[kMaxChains]{};
+    StepArgs chain_args[kMaxChains]{};          // chunk views of the one group
+    std::vector<int> chain_groups[kMaxChains];  // the groups of each chain of a multi-mesh batch
     cudaStream_t chain_stream[kMaxChains - 1] = {};
     cudaEvent_t chain_ev[kMaxChains] = {};
 };
@@ -195,10 +196,12 @@ int setup_grouped_gemm(bpm_batch* bt) {
 int setup_chains(bpm_batch* bt) {
     for (auto& h : bt->gg_chain) grouped_gemm_free(&h);
     bt->chains = 0;
-    if (bt->streams < 2 || !tensor_core_precision(bt) || bt->groups.size() != 1) return BPM_OK;
-    Group& g = bt->groups[0];
-    const int chunk = kIslandPad * ((g.B + bt->streams * kIslandPad - 1) / (bt->streams * kIslandPad));
-    const int chains = (g.B + chunk - 1) / chunk;
+    for (auto& v : bt->chain_groups) v.clear();
+    if (bt->streams < 2 || !tensor_core_precision(bt)) return BPM_OK;
+    const int ng = (int)bt->groups.size();
+    const int chunk = ng > 1 ? 0 : kIslandPad * ((bt->groups[0].B + bt->streams * kIslandPad - 1) /
+                                                 (bt->streams * kIslandPad));
+    const int chains = ng > 1 ? std::min(bt->streams, ng) : (bt->groups[0].B + chunk - 1) / chunk;
     if (chains < 2) return BPM_OK;
     for (int c = 0; c < kMaxChains - 1; ++c)
         if (!bt->chain_stream[c] && cudaStreamCreateWithFlags(&bt->chain_stream[c], cudaStreamNonBlocking) !=
@@ -211,6 +214,34 @@ int setup_chains(bpm_batch* bt) {
             set_error("event creation failed");
             return BPM_ERR_CUDA;
         }
+    const int products = bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1;
+    if (ng > 1) {
+        // a multi-mesh batch: its groups dealt to the chains, largest GEMM first, each to the chain
+        // with the least GEMM work so far (rows x K^2)
+        std::vector<int> order(ng);
+        for (int i = 0; i < ng; ++i) order[i] = i;
+        auto work = [&](int i) { return (double)bt->groups[i].Bp * bt->groups[i].mesh->K() * bt->groups[i].mesh->K(); };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+        std::vector<double> load(chains, 0.0);
+        for (int i : order) {
+            const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            bt->chain_groups[c].push_back(i);
+            load[c] += work(i);
+        }
+        for (int c = 0; c < chains; ++c) {
+            std::vector<GemmOperands> ops;
+            for (int i : bt->chain_groups[c]) {
+                const Group& q = bt->groups[i];
+                const int K = q.mesh->K();
+                ops.push_back(GemmOperands{q.Ahi, q.Alo, q.mesh->Nhi, q.mesh->Nlo, q.Hd, q.Bp, K, K});
+            }
+            BPM_TRY(grouped_gemm_setup(&bt->gg_chain[c], ops, bt->tile_n, products, bt->raster, bt->k_block,
+                                       bt->ctx->l2_bytes, bt->pair));
+        }
+        bt->chains = chains;
+        return BPM_OK;
+    }
+    Group& g = bt->groups[0];
     const int K = g.mesh->K();
     for (int c = 0; c < chains; ++c) {
         const int b0 = c * chunk;
@@ -218,8 +249,8 @@ int setup_chains(bpm_batch* bt) {
         const size_t off = (size_t)b0 * K, S = (size_t)b0 * 3 * g.mesh->n_pad;
         std::vector<GemmOperands> ops{GemmOperands{g.Ahi + off, g.Alo + off, g.mesh->Nhi, g.mesh->Nlo, g.Hd + off,
                                                    rows, K, K}};
-        BPM_TRY(grouped_gemm_setup(&bt->gg_chain[c], ops, bt->tile_n, bt->p.precision == BPM_PREC_BF16X3 ? 3 : 1,
-                                   bt->raster, bt->k_block, bt->ctx->l2_bytes, bt->pair));
+        BPM_TRY(grouped_gemm_setup(&bt->gg_chain[c], ops, bt->tile_n, products, bt->raster, bt->k_block,
+                                   bt->ctx->l2_bytes, bt->pair));
         StepArgs a = g.args;
         a.B = std::min(chunk, g.B - b0);
         a.isl += 3 * (size_t)b0;
@@ -285,13 +316,18 @@ struct StageLaunches {
     int threads = 256;
 };
 
-int build_stage_launches(const bpm_batch* bt, StageLaunches* out) {
+int build_stage_launches(const bpm_batch* bt, StageLaunches* out, const std::vector<int>* subset = nullptr) {
     out->launch.clear();
     out->smem.clear();
     out->threads = bt->groups[0].args.threads;
     const int ipb = stage_islands_per_cta(bt->groups[0].args);
-    std::vector<int> order(bt->groups.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::vector<int> order;
+    if (subset) {
+        order = *subset;
+    } else {
+        order.resize(bt->groups.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    }
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         return bt->groups[x].mesh->n_pad > bt->groups[y].mesh->n_pad;
     });
@@ -344,11 +380,23 @@ int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
         for (int c = 1; c < bt->chains; ++c) BPM_CK(cudaStreamWaitEvent(bt->chain_stream[c - 1], bt->chain_ev[0], 0));
         for (int c = 0; c < bt->chains; ++c) {
             cudaStream_t sc = c ? bt->chain_stream[c - 1] : s;
+            // a chunk of the one group, one group of a multi-mesh batch, or several groups (one
+            // stage launch per occupancy class, as for the whole batch)
+            const std::vector<int>& cg = bt->chain_groups[c];
+            StageLaunches L;
+            if (cg.size() > 1) BPM_TRY(build_stage_launches(bt, &L, &cg));
+            const StepArgs& one = cg.empty() ? bt->chain_args[c] : bt->groups[cg[0]].args;
             for (int j = 0; j < bt->p.substeps; ++j) {
-                BPM_TRY(grouped_gemm_launch(sc, bt->gg_chain[c], bt->ctx->sm_count, bt->gemm_err));
-                launch_stage1(bt->chain_args[c], j, sc);
-                BPM_TRY(grouped_gemm_launch(sc, bt->gg_chain[c], bt->ctx->sm_count, bt->gemm_err));
-                launch_stage2(bt->chain_args[c], j, sc);
+                for (int k = 1; k <= 2; ++k) {
+                    BPM_TRY(grouped_gemm_launch(sc, bt->gg_chain[c], bt->ctx->sm_count, bt->gemm_err));
+                    if (cg.size() > 1) {
+                        for (size_t q = 0; q < L.launch.size(); ++q)
+                            (k == 1 ? launch_stage1_groups : launch_stage2_groups)(L.launch[q], L.threads, L.smem[q],
+                                                                                   j, sc);
+                    } else {
+                        (k == 1 ? launch_stage1 : launch_stage2)(one, j, sc);
+                    }
+                }
             }
         }
         for (int c = 1; c < bt->chains; ++c) {
@@ -879,6 +927,9 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         if (r != BPM_OK) set_error("stream/event creation failed");
     }
     if (r == BPM_OK && tensor_core_precision(bt)) r = setup_grouped_gemm(bt);
+    // two chains by default for a one-mesh batch; a multi-mesh batch starts as one chain (dealing
+    // its groups to chains measured slower on the uneven batch: more stage launches per interval)
+    bt->streams = bt->groups.size() == 1 ? 2 : 1;
     if (r == BPM_OK) r = setup_chains(bt);
     if (r != BPM_OK) {
         free_batch(bt);
@@ -1291,7 +1342,7 @@ int bpm_batch_autotune(bpm_batch* bt, int32_t reps, bpm_tuning* chosen) {
     }
     // one chain or several: whole intervals of the interval graph, where several chains apply
     int bt_s = 1;
-    if (tensor_core_precision(bt) && bt->groups.size() == 1 && bt->groups[0].B > kIslandPad) {
+    if (tensor_core_precision(bt) && (bt->groups.size() > 1 || bt->groups[0].B > kIslandPad)) {
         double best_i = 1e300;
         for (int ns = 1; ns <= kMaxChains; ++ns) {
             bpm_tuning t{bt_n, bt_t, bt_r, bt_i, bt_k, bt_p, ns, 0, 0};

@@ -278,6 +278,23 @@ def test_two_stream_intervals_give_the_same_states(ctx, small, headmap):
                    map_id=hid) as bt:
         t = bt.autotune(reps=2)
         assert t["streams"] in (1, 2, 3, 4)
+    # a batch of three meshes: its groups dealt to two or three chains
+    mid2 = ctx.mesh_upload(synth.layered_island_mesh(7.0, 6.0, 4.0, rings=2, hard_slabs=9, soft_slabs=6, seed=5),
+                           mats)
+    mid3 = ctx.mesh_upload(synth.layered_island_mesh(6.0, 5.0, 3.0, rings=2, hard_slabs=7, soft_slabs=4, seed=6),
+                           mats)
+    isl = synth.Islands.concat([synth.jittered_islands(101, seed=73, mesh_id=mid),
+                                synth.jittered_islands(200, seed=74, mesh_id=mid2),
+                                synth.jittered_islands(57, seed=75, mesh_id=mid3)])
+    outs = []
+    for streams in (1, 2, 4):
+        with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+            bt.set_tuning(256, 256, L.RASTER_AUTO, 2, 32, streams=streams)
+            bt.advance(20)
+            outs.append(bt.read())
+    for o in outs[1:]:
+        for key in ("m", "switched", "t_sw", "mz", "status"):
+            assert np.array_equal(o[key], outs[0][key]), key
 
 
 def test_two_islands_per_cta_odd_groups(ctx, small, headmap):
