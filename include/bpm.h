@@ -489,9 +489,9 @@ int bpm_surrogate_destroy(bpm_ctx* ctx, int32_t sid);
  * Requests whose scratch would exceed the array (about 60*B*n_pad bytes, e.g.
  * 80 islands of a 1547-node mesh) fail with BPM_ERR_ARG and a message giving
  * the size needed.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array, which keeps the previous call's
- * contents (each call clears the region it uses): calls that overlap on the
+ * address (cudaGetSymbolAddress).  All calls share the one array, which keeps
+ * the previous call's contents (each call clears the region it uses): calls
+ * that overlap on the
  * GPU -- on different streams or contexts of the same device -- race and
  * corrupt each other.  Work is ordered on the context's stream; the call does
  * not synchronise. */
