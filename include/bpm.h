@@ -491,9 +491,8 @@ int bpm_surrogate_destroy(bpm_ctx* ctx, int32_t sid);
  * the size needed.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress).  All calls share the one array, which keeps
  * the previous call's contents (each call clears the region it uses): calls
- * that overlap on the
- * GPU -- on different streams or contexts of the same device -- race and
- * corrupt each other.  Work is ordered on the context's stream; the call does
+ * that overlap on the GPU -- on different streams or contexts of the same
+ * device -- race and corrupt each other.  Work is ordered on the context's stream; the call does
  * not synchronise. */
 int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int32_t B,
                             const bpm_run_params* p, int32_t n_intervals, float* m, int32_t ld,
