@@ -381,6 +381,15 @@ def measure_head_field(ctx, nx=64, ny=64, nz=18, reps=20):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     B = out.cpu().numpy()
+    # with Table I's initial trailing shield (9 nm gap, 10 nm thick, 2 nm panels): the boundary-
+    # element solve (matrix, LU, triangular solves, residual check) and the field, one call
+    gs = dict(g, trailing_shield_gap_nm=9.0, shield_thickness_nm=10.0, shield_panel_nm=2.0)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ctx.head_field(gs, nx, ny, nz, 1.0, org, out=out)
+    torch.cuda.synchronize()
+    ms_shield = (time.perf_counter() - t) * 1e3
+    Bs = out.cpu().numpy()
     # the oracle's quadrature on a bounded sample of voxels
     from oracle import polefield
     pts = np.array([[-10.0, 0.0, 17.0], [0.0, 7.0, 17.0], [-30.0, 20.0, 5.0], [5.0, -10.0, 12.0]])
@@ -389,6 +398,12 @@ def measure_head_field(ctx, nx=64, ny=64, nz=18, reps=20):
     o_vox = len(pts) / (time.perf_counter() - t)
     return {"voxels": nx * ny * nz, "ms_per_map": ms, "voxels_per_s": nx * ny * nz / (ms * 1e-3),
             "triangles": 24, "peak_under_pole_T": float(B[17, 32, 38, 2]),
+            "with_trailing_shield": {"ms_per_map": ms_shield, "gap_nm": 9.0, "thickness_nm": 10.0, "panel_nm": 2.0,
+                                     "under_pole_T": float(Bs[17, 32, 38, 2]),
+                                     "trailing_edge_T": [float(v) for v in Bs[17, 32, 48]],
+                                     "trailing_edge_without_T": [float(v) for v in B[17, 32, 48]],
+                                     "note": "wall-clock of one call: panel matrix, LU and solves on the GPU, "
+                                             "residual check, field of pole, shield and images"},
             "form": "saturated CoFe main pole (Table I initial design) as surface charges, charge sheet at the "
                     "yoke edge, under-layer image; closed form per triangle, FP64, one thread per voxel",
             "cpu_baseline": {"voxels_per_s": o_vox, "kind": "oracle", "cores": 1,

@@ -203,7 +203,10 @@ typedef struct {
     float z_abs_nm;                /* ABS height in the map frame */
     float z_sul_nm;                /* upper surface of the soft under-layer, below the map */
     int32_t sul_image;             /* 1: mirror the pole in the under-layer; 0: no under-layer */
-    float reserved[2];
+    float trailing_shield_gap_nm;  /* Table I: 5 .. 20 nm; 0: no trailing shield */
+    float shield_thickness_nm;     /* Table I: 3 .. 20 nm, the shield's height above the ABS */
+    float shield_panel_nm;         /* edge length of the shield's boundary-element panels (0: 2 nm) */
+    float reserved;
 } bpm_pole_geometry;
 
 /* Field mu0*H (tesla) of the saturated main pole on a voxel grid: the pole is
@@ -211,15 +214,27 @@ typedef struct {
  * surface charges Js n_z on its faces (the face at the yoke edge is the charge
  * sheet that stands in for the yoke, return pole and coil); a soft under-layer
  * of unbounded permeability is the pole's mirror image in z = z_sul_nm with
- * charges of the opposite sign.  Each triangle's field is evaluated in closed
- * form (its solid angle along the normal plus a logarithm per edge) in FP64.
- * Shields are not modelled.
+ * charges of the opposite sign.
+ * With trailing_shield_gap_nm > 0 a trailing shield of unbounded permeability
+ * responds to the pole: a block whose leading face is parallel to the pole's
+ * trailing face at that gap (down-track, at the ABS), standing on the ABS,
+ * shield_thickness_nm high, 30 nm deep down-track and 40 nm wider than the
+ * pole tip on each side.  Its surface is an equipotential of the magnetic
+ * potential and carries no net charge: a boundary-element solve for a uniform
+ * charge on each of its triangular panels (collocation at the panel
+ * centroids, the panel potentials in closed form, the under-layer image of the
+ * shield included), by LU factorisation on the GPU in FP64.  Side shields are
+ * not modelled.
+ * Each triangle's field is evaluated in closed form (its solid angle along the
+ * normal plus a logarithm per edge) in FP64.
  *   B_T  [nz][ny][nx][3] float32: voxel (ix, iy, iz) at origin + h (ix, iy, iz);
  *        host memory, or device memory of the context when on_device is 1
  *        (written in stream order on the context stream)
  * BPM_ERR_ARG for a bad geometry (non-positive sizes or Js, angles outside
- * [0, 80) deg, a taper outside (0, 90] deg, z_sul above the ABS) or a grid
- * that reaches the ABS or, with the image, the under-layer. */
+ * [0, 80) deg, a taper outside (0, 90] deg, z_sul above the ABS, a shield
+ * without thickness, panels below 0.5 nm or more than 6144 of them) or a grid
+ * that reaches the ABS or, with the image, the under-layer;
+ * BPM_ERR_UNSTABLE if the shield solve's residual exceeds 1e-8 of its scale. */
 int bpm_head_field_solve(bpm_ctx* ctx, const bpm_pole_geometry* g, int32_t nx, int32_t ny, int32_t nz,
                          float h_nm, const float origin_nm[3], float* B_T, int on_device);
 

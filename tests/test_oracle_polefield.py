@@ -120,3 +120,89 @@ def test_geometry_readings():
     abs_tris = np.all(np.isclose(tris[:12, :, 2], g["z_abs_nm"]), axis=1)
     top_tris = np.all(np.isclose(tris[:12, :, 2], g["z_abs_nm"] + H), axis=1)
     assert np.allclose(q[:12][abs_tris], 2.4) and np.allclose(q[:12][top_tris], -2.4)
+
+
+def test_closed_form_panel_potential_against_quadrature():
+    # the oracle's closed-form panel potential (the shield solve's matrix entries) against the
+    # quadrature of the same integral: on the triangle, beside it, above and below, far away
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        tri = rng.uniform(-3, 3, (3, 3))
+        cent = tri.mean(axis=0)
+        n = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+        n /= np.linalg.norm(n)
+        for P in (cent, cent + 0.3 * n, cent - 2.0 * n, tri[0] + 0.5 * (tri[1] - tri[0]) + 1e-3 * n,
+                  tri[1] + 2.0 * (tri[1] - tri[2]), cent + 20.0 * rng.normal(size=3)):
+            want = polefield._potential(tri, P, ratio=0.1)
+            got = polefield.potential_closed(tri[None], P)[0]
+            assert abs(got - want) <= 1e-9 * abs(want), (P, got, want)
+
+
+def _icosphere(level, radius):
+    t = (1 + math.sqrt(5)) / 2
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    v = [np.array(p, float) / np.linalg.norm(p) for p in v]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        cache, nf = {}, []
+
+        def mid(i, j):
+            key = (min(i, j), max(i, j))
+            if key not in cache:
+                m = v[i] + v[j]
+                v.append(m / np.linalg.norm(m))
+                cache[key] = len(v) - 1
+            return cache[key]
+        for a, b, c in f:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        f = nf
+    tris = np.array([[radius * v[i] for i in tri] for tri in f])
+    for k, tr in enumerate(tris):                      # outward winding
+        if np.dot(np.cross(tr[1] - tr[0], tr[2] - tr[0]), tr.mean(axis=0)) < 0:
+            tris[k] = tr[[0, 2, 1]]
+    areas = 0.5 * np.linalg.norm(np.cross(tris[:, 1] - tris[:, 0], tris[:, 2] - tris[:, 0]), axis=1)
+    return tris, areas
+
+
+def test_soft_sphere_in_a_uniform_field():
+    # a sphere of unbounded permeability in a uniform field B0 z: the surface is an equipotential
+    # with no net charge, and the induced charge (3 B0 cos theta) has the dipole moment
+    # 4 pi a^3 B0 (the field outside is B0 plus that dipole's); the error of the flat panels falls
+    # with refinement
+    a, B0 = 10.0, 0.5
+    errs = []
+    for level in (2, 3):
+        tris, areas = _icosphere(level, a)
+        cent = tris.mean(axis=1)
+        q, Phi = polefield.bem_equipotential(tris, areas, -B0 * cent[:, 2])
+        moment = (q[:, None] * areas[:, None] * cent).sum(axis=0)
+        want = 4 * math.pi * a ** 3 * B0
+        errs.append(abs(moment[2] - want) / want)
+        assert abs(Phi) <= 1e-9 and np.abs(moment[:2]).max() <= 1e-6 * want
+        assert abs((q * areas).sum()) <= 1e-9 * want / a
+    print("sphere moment errors", errs)
+    assert errs[0] / errs[1] > 3.0 and errs[1] <= 0.011    # second order in the panel size
+
+
+def test_shield_interior_is_at_the_shield_potential():
+    # the solved shield: inside a closed equipotential surface the potential is that constant;
+    # the pole's potential plus the shield's (and the images') at interior points of the block
+    g = synth.pole_geometry(trailing_shield_gap_nm=9.0, shield_thickness_nm=10.0, shield_panel_nm=3.0)
+    tris, q, Phi = polefield.shield_charges(g)
+    areas = polefield.shield_panels(g)[1]
+    assert abs((q * areas).sum()) <= 1e-9 * np.abs(q * areas).sum()
+    img = tris.copy()
+    img[..., 2] = 2 * g["z_sul_nm"] - img[..., 2]
+    img = img[:, [0, 2, 1]]
+    tt = math.tan(math.radians(g["trailing_edge_angle_deg"]))
+    inner = [np.array([9.0 + 15.0 + 5.0 * tt, y, g["z_abs_nm"] + 5.0]) for y in (-30.0, 0.0, 20.0)]
+    pole_phi = polefield.pole_potential(g, np.array(inner))
+    for P, pp in zip(inner, pole_phi):
+        shield_phi = ((polefield.potential_closed(tris, P) - polefield.potential_closed(img, P)) * q).sum() / (4 * math.pi)
+        assert abs(pp + shield_phi - Phi) <= 2e-3 * abs(Phi), (pp + shield_phi, Phi)
+    # the pole drives the shield: its potential is not the under-layer's (zero)
+    assert abs(Phi) > 0.1
