@@ -23,7 +23,8 @@ Readings (where the paper gives no number or formula):
 * the SUL has unbounded permeability: the magnetic potential is constant on
   its surface, which the mirror image of the pole with charges of the
   opposite sign gives;
-* shields are not modelled.
+* the trailing shield (when its gap is given) is solved as described below;
+  side shields are not modelled.
 
 The field is evaluated by numerical quadrature of the Coulomb integral
     mu0 H(P) = (Js (m . n) / 4 pi) int (P - Q) / |P - Q|^3 dA_Q

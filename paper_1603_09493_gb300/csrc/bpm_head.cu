@@ -17,8 +17,14 @@
 // magnetic potential constant on its surface; the pole's mirror image in that
 // plane, with charges of the opposite sign, reproduces it.
 //
-// One thread per voxel, FP64 over every triangle of the pole and its image (at
-// most 24), the result stored as float32 mu0 H in tesla.
+// A trailing shield of unbounded permeability (when its gap is given) keeps its
+// surface at one magnetic potential and carries no net charge: its triangular
+// panels get the uniform charges that satisfy this at their centroids
+// (collocation), from a dense system of closed-form panel potentials factored
+// by LU on the GPU in FP64.
+//
+// The field: one thread per voxel, FP64 over every triangle of the pole, the
+// shield and their images, stored as float32 mu0 H in tesla.
 #include <algorithm>
 #include <cmath>
 #include <utility>
