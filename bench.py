@@ -578,6 +578,44 @@ def main_surrogate_study(args):
     return 0
 
 
+def main_paper_loop(args):
+    """The paper's optimisation loop (Sec. II.A, Fig. 4) on the GPU: every design's head field
+    is solved from its Table I geometry (pole, charge sheet, trailing shield, under-layer), its
+    target and previous bits go through the critical-field searches, its adjacent-track bit
+    through the NEB barrier, and EGO (maximin Latin hypercube, kriging, expected improvement)
+    proposes the next design from log10(BER_tot); one JSON line."""
+    import torch
+    from paper_1603_09493_gb300 import api, model
+    torch.cuda.set_device(0)
+    ctx = api.Context(0, stream=torch.cuda.Stream())
+    keys = ["trailing_shield_gap_nm", "trailing_edge_angle_deg", "side_edge_angle_deg", "pole_tip_width_nm",
+            "shield_thickness_nm", "K1_hard_MJ_m3", "A_ex_int_pJ_m", "down_track_offset_nm"]
+    t = time.perf_counter()
+    init = model.evaluate(ctx, model.initial_design(), layout=args.loop_layout)
+    t_init = time.perf_counter() - t
+    print(json.dumps({"initial_design": init}), file=sys.stderr, flush=True)
+    t = time.perf_counter()
+    res = model.optimise(ctx, keys, args.loop_init, args.loop_iters, seed=1, layout=args.loop_layout,
+                         log=lambda r: print(json.dumps({k: r[k] for k in ("ber_tot", "ber_targ", "ber_prev",
+                                                                            "ber_adj", "unit")}),
+                                             file=sys.stderr, flush=True))
+    t_loop = time.perf_counter() - t
+    y = res["log10_ber_tot"]
+    best_so_far = np.minimum.accumulate(y).tolist()
+    ctx.close()
+    print(json.dumps({
+        "workload": "paper loop: Table I design -> solved head field -> critical-field searches -> NEB -> BER_tot, "
+                    f"EGO over {len(keys)} parameters, {args.loop_layout} layout",
+        "free_parameters": keys, "initial_design": init, "initial_seconds": t_init,
+        "lhs_designs": args.loop_init, "ego_iterations": args.loop_iters,
+        "log10_ber_tot": [float(v) for v in y], "best_so_far": best_so_far,
+        "best_design": res["best"], "best_log10_ber_tot": res["best_log10_ber_tot"],
+        "max_ei": res["max_ei"], "space_filling_steps": res["space_filling_steps"],
+        "designs_writing_the_target": int(sum(not r["aborted"] for r in res["evaluations"])),
+        "seconds": t_loop, "seconds_per_design": t_loop / len(y)}))
+    return 0
+
+
 def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -724,6 +762,8 @@ def main(args):
         return main_extras(args)
     if args.workload == "surrogate-study":
         return main_surrogate_study(args)
+    if args.workload == "paper-loop":
+        return main_paper_loop(args)
     import torch
     from paper_1603_09493_gb300 import _lib as L
     from paper_1603_09493_gb300 import api, synth
@@ -893,9 +933,12 @@ if __name__ == "__main__":
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--gemm-pair", action="store_true", help="run the demag GEMM on CTA pairs (no autotune)")
     ap.add_argument("--workload", default="census",
-                    choices=["census", "uneven", "extras", "surrogate", "surrogate-study"])
+                    choices=["census", "uneven", "extras", "surrogate", "surrogate-study", "paper-loop"])
     ap.add_argument("--study-round", type=int, default=32768, help="labels per round of the surrogate study")
     ap.add_argument("--study-rounds", type=int, default=4)
+    ap.add_argument("--loop-init", type=int, default=16, help="Latin-hypercube designs of the paper loop")
+    ap.add_argument("--loop-iters", type=int, default=16, help="EGO iterations of the paper loop")
+    ap.add_argument("--loop-layout", default="staggered", choices=["centered", "staggered", "shingled"])
     ap.add_argument("--realisations", type=int, default=512)
     ap.add_argument("--clock-log", default="", help="also write the raw nvidia-smi clock samples here")
     sys.exit(main(ap.parse_args()))

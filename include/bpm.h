@@ -103,7 +103,7 @@ typedef struct {
     double   t0_ps;       /* start time */
     double   alpha;       /* Gilbert damping */
     double   rise_ps;     /* linear rise of head and uniform field, ramp = min(1, t/rise); <= 0: none */
-    double   v_m_per_s;   /* head velocity along +x */
+    double   v_m_per_s;   /* head velocity along +x (signed: < 0 moves the head along -x) */
     double   x0_nm;       /* head position at t = 0 */
     int32_t  map_id;      /* head map from bpm_headmap_upload, or -1 */
     uint32_t term_mask;   /* BPM_TERM_* */
