@@ -206,7 +206,7 @@ typedef struct {
     float trailing_shield_gap_nm;  /* Table I: 5 .. 20 nm; 0: no trailing shield */
     float shield_thickness_nm;     /* Table I: 3 .. 20 nm, the shield's height above the ABS */
     float shield_panel_nm;         /* edge length of the shield's boundary-element panels (0: 2 nm) */
-    float reserved;
+    float side_shield_gap_nm;      /* Table I: 5 .. 20 nm; 0: no side shields */
 } bpm_pole_geometry;
 
 /* Field mu0*H (tesla) of the saturated main pole on a voxel grid: the pole is
@@ -223,8 +223,11 @@ typedef struct {
  * potential and carries no net charge: a boundary-element solve for a uniform
  * charge on each of its triangular panels (collocation at the panel
  * centroids, the panel potentials in closed form, the under-layer image of the
- * shield included), by LU factorisation on the GPU in FP64.  Side shields are
- * not modelled.
+ * shield included), by LU factorisation on the GPU in FP64.  With
+ * side_shield_gap_nm > 0 two side shields join it as one body: blocks whose
+ * inner faces are parallel to the pole's flared sides at that gap, as high as
+ * the trailing shield, from 10 nm behind the leading edge to 0.5 nm short of
+ * the trailing shield, out to its cross-track extent.
  * Each triangle's field is evaluated in closed form (its solid angle along the
  * normal plus a logarithm per edge) in FP64.
  *   B_T  [nz][ny][nx][3] float32: voxel (ix, iy, iz) at origin + h (ix, iy, iz);
@@ -232,7 +235,8 @@ typedef struct {
  *        (written in stream order on the context stream)
  * BPM_ERR_ARG for a bad geometry (non-positive sizes or Js, angles outside
  * [0, 80) deg, a taper outside (0, 90] deg, z_sul above the ABS, a shield
- * without thickness, panels below 0.5 nm or more than 6144 of them) or a grid
+ * without thickness, a side gap of 40 nm or more, panels below 0.5 nm or more
+ * than 6144 of them) or a grid
  * that reaches the ABS or, with the image, the under-layer;
  * BPM_ERR_UNSTABLE if the shield solve's residual exceeds 1e-8 of its scale. */
 int bpm_head_field_solve(bpm_ctx* ctx, const bpm_pole_geometry* g, int32_t nx, int32_t ny, int32_t nz,

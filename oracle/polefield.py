@@ -23,8 +23,8 @@ Readings (where the paper gives no number or formula):
 * the SUL has unbounded permeability: the magnetic potential is constant on
   its surface, which the mirror image of the pole with charges of the
   opposite sign gives;
-* the trailing shield (when its gap is given) is solved as described below;
-  side shields are not modelled.
+* the shield (trailing and side blocks, when their gaps are given) is solved
+  as described below.
 
 The field is evaluated by numerical quadrature of the Coulomb integral
     mu0 H(P) = (Js (m . n) / 4 pi) int (P - Q) / |P - Q|^3 dA_Q
@@ -144,46 +144,79 @@ def field_map(g: dict, nx: int, ny: int, nz: int, h_nm: float, origin_nm) -> np.
 
 
 # --------------------------------------------------------------------------------------------
-# Trailing shield (Sec. II.A wrap-around shield, Table I gap and thickness).  Readings: the
-# shield has unbounded permeability, so its surface is an equipotential of the magnetic
-# potential and it carries no net magnetic charge; only the trailing part is modelled, as a
-# block standing on the ABS whose leading face is parallel to the pole's trailing face at the
-# trailing shield gap (down-track, at the ABS), shield_thickness_nm high (Table I's shield
-# thickness read as the height above the ABS), 30 nm deep down-track and 40 nm wider than the
-# pole tip on each side.  Its surface is cut into flat triangles carrying uniform charge
-# (collocation at the triangle centroids), and the under-layer image applies to them too.
+# Wrap-around shield (Sec. II.A, Table I gaps and thickness).  Readings: the shield has unbounded
+# permeability, so its surface is an equipotential of the magnetic potential and it carries no
+# net magnetic charge.  Its trailing block stands on the ABS with its leading face parallel to
+# the pole's trailing face at the trailing shield gap (down-track, at the ABS),
+# shield_thickness_nm high (Table I's shield thickness read as the height above the ABS), 30 nm
+# deep down-track and 40 nm wider than the pole tip on each side; each side block has its inner
+# face parallel to the pole's flared side at the side shield gap, as high, from 10 nm behind the
+# leading edge to 0.5 nm short of the trailing block, out to the trailing block's extent.  The
+# surface is cut into flat triangles carrying uniform charge (collocation at the triangle
+# centroids), and the under-layer image applies to them too.
 # --------------------------------------------------------------------------------------------
 
 SHIELD_DEPTH_NM = 30.0
 SHIELD_MARGIN_NM = 40.0
+SIDE_LEAD_NM = 10.0        # side shields start this far behind the leading edge
+SIDE_CLEAR_NM = 0.5        # and stop this far short of the trailing shield
+
+
+def shield_blocks(g: dict):
+    """The shield's blocks as (corner, three edge vectors): the trailing block, and with a side
+    shield gap the two side blocks, whose inner faces lean out with the pole's flared sides (the
+    paper builds every shield face parallel to the opposite pole face); one body."""
+    tt = math.tan(math.radians(g["trailing_edge_angle_deg"]))
+    ts = math.tan(math.radians(g["side_edge_angle_deg"]))
+    w = float(g["pole_tip_width_nm"])
+    W = w + 2 * SHIELD_MARGIN_NM
+    T = float(g["shield_thickness_nm"])
+    z0 = float(g["z_abs_nm"])
+    gap_t = float(g.get("trailing_shield_gap_nm", 0.0))
+    gap_s = float(g.get("side_shield_gap_nm", 0.0))
+    blocks = []
+    if gap_t > 0:
+        blocks.append((np.array([gap_t, -W / 2, z0]), np.array([SHIELD_DEPTH_NM, 0, 0]), np.array([0, W, 0]),
+                       np.array([T * tt, 0, T])))
+    if gap_s > 0:
+        x0 = -float(g["abs_thickness_nm"]) - SIDE_LEAD_NM
+        x1 = max(gap_t, 0.0) - SIDE_CLEAR_NM
+        inner = w / 2 + gap_s
+        reach = W / 2 - inner
+        blocks.append((np.array([x0, inner, z0]), np.array([x1 - x0, 0, 0]), np.array([0, reach, 0]),
+                       np.array([0, T * ts, T])))
+        blocks.append((np.array([x0, -W / 2, z0]), np.array([x1 - x0, 0, 0]), np.array([0, reach, 0]),
+                       np.array([0, -T * ts, T])))
+    return blocks
+
+
+def has_shield(g: dict) -> bool:
+    return float(g.get("trailing_shield_gap_nm", 0.0)) > 0 or float(g.get("side_shield_gap_nm", 0.0)) > 0
 
 
 def shield_panels(g: dict):
-    """Triangles [N][3][3] of the shield block (outward winding) and their areas [N]: each face a
-    grid of about shield_panel_nm squares (parallelograms), each cell split along the diagonal
+    """Triangles [N][3][3] of the shield's blocks (outward winding) and their areas [N]: each face
+    a grid of about shield_panel_nm squares (parallelograms), each cell split along the diagonal
     from its first corner."""
     panel = float(g.get("shield_panel_nm") or 2.0)
-    tt = math.tan(math.radians(g["trailing_edge_angle_deg"]))
-    W = float(g["pole_tip_width_nm"]) + 2 * SHIELD_MARGIN_NM
-    T = float(g["shield_thickness_nm"])
-    corner = np.array([float(g["trailing_shield_gap_nm"]), -W / 2, float(g["z_abs_nm"])])
-    dx, dy, dz = np.array([SHIELD_DEPTH_NM, 0, 0]), np.array([0, W, 0]), np.array([T * tt, 0, T])
-    centre = corner + (dx + dy + dz) / 2
-    faces = [(corner, dx, dy), (corner + dz, dx, dy), (corner, dy, dz), (corner + dx, dy, dz),
-             (corner, dx, dz), (corner + dy, dx, dz)]
     tris, areas = [], []
-    for origin, u, v in faces:
-        nu = max(1, math.ceil(np.linalg.norm(u) / panel - 1e-9))
-        nv = max(1, math.ceil(np.linalg.norm(v) / panel - 1e-9))
-        for i in range(nu):
-            for j in range(nv):
-                p = lambda a, b: origin + (a / nu) * u + (b / nv) * v
-                for a, b, c in ((p(i, j), p(i + 1, j), p(i + 1, j + 1)), (p(i, j), p(i + 1, j + 1), p(i, j + 1))):
-                    n = np.cross(b - a, c - a)
-                    if np.dot(n, (a + b + c) / 3 - centre) < 0:
-                        b, c = c, b
-                    tris.append(np.array([a, b, c]))
-                    areas.append(0.5 * np.linalg.norm(n))
+    for corner, dx, dy, dz in shield_blocks(g):
+        centre = corner + (dx + dy + dz) / 2
+        faces = [(corner, dx, dy), (corner + dz, dx, dy), (corner, dy, dz), (corner + dx, dy, dz),
+                 (corner, dx, dz), (corner + dy, dx, dz)]
+        for origin, u, v in faces:
+            nu = max(1, math.ceil(np.linalg.norm(u) / panel - 1e-9))
+            nv = max(1, math.ceil(np.linalg.norm(v) / panel - 1e-9))
+            for i in range(nu):
+                for j in range(nv):
+                    p = lambda a, b: origin + (a / nu) * u + (b / nv) * v
+                    for a, b, c in ((p(i, j), p(i + 1, j), p(i + 1, j + 1)),
+                                    (p(i, j), p(i + 1, j + 1), p(i, j + 1))):
+                        n = np.cross(b - a, c - a)
+                        if np.dot(n, (a + b + c) / 3 - centre) < 0:
+                            b, c = c, b
+                        tris.append(np.array([a, b, c]))
+                        areas.append(0.5 * np.linalg.norm(n))
     return np.array(tris), np.array(areas)
 
 
@@ -338,7 +371,7 @@ def field_with_shield(g: dict, points_nm: np.ndarray) -> np.ndarray:
     """mu0 H (tesla) of the pole and, when g has a trailing shield gap, the shield's induced
     charges (and their images), at points [..., 3] (nm)."""
     B = field(g, points_nm)
-    if not float(g.get("trailing_shield_gap_nm", 0.0)) > 0:
+    if not has_shield(g):
         return B
     tris, q, _ = shield_charges(g)
     if g.get("sul_image", 0):

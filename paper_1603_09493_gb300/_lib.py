@@ -73,7 +73,7 @@ class bpm_pole_geometry(ctypes.Structure):
                 ("side_edge_angle_deg", c_float), ("taper_angle_deg", c_float), ("abs_thickness_nm", c_float),
                 ("yoke_edge_nm", c_float), ("Js_T", c_float), ("z_abs_nm", c_float), ("z_sul_nm", c_float),
                 ("sul_image", c_int32), ("trailing_shield_gap_nm", c_float), ("shield_thickness_nm", c_float),
-                ("shield_panel_nm", c_float), ("reserved", c_float)]
+                ("shield_panel_nm", c_float), ("side_shield_gap_nm", c_float)]
 
 
 class bpm_tuning(ctypes.Structure):

@@ -148,8 +148,7 @@ class Context:
         from . import synth
         g = L.bpm_pole_geometry()
         for f, _ in L.bpm_pole_geometry._fields_:
-            if f != "reserved":
-                setattr(g, f, type(getattr(g, f))(geometry[f]))
+            setattr(g, f, type(getattr(g, f))(geometry.get(f, 0)))
         org = np.ascontiguousarray(origin_nm, np.float32)
         if out is not None:
             with self.device_order():

@@ -17,8 +17,9 @@
 // magnetic potential constant on its surface; the pole's mirror image in that
 // plane, with charges of the opposite sign, reproduces it.
 //
-// A trailing shield of unbounded permeability (when its gap is given) keeps its
-// surface at one magnetic potential and carries no net charge: its triangular
+// A wrap-around shield of unbounded permeability (trailing and side blocks, when
+// their gaps are given) keeps its surface at one magnetic potential and carries
+// no net charge: its triangular
 // panels get the uniform charges that satisfy this at their centroids
 // (collocation), from a dense system of closed-form panel potentials factored
 // by LU on the GPU in FP64.
@@ -368,47 +369,67 @@ int pole_triangles(const bpm_pole_geometry& g, HeadTris* T) {
     return BPM_OK;
 }
 
-// Panels of the trailing shield: a block standing on the ABS whose leading face is parallel to
+// Panels of the shield: the trailing block stands on the ABS with its leading face parallel to
 // the pole's trailing face at the gap, shield_thickness high, kShieldDepth deep down-track and
 // kShieldMargin wider than the pole tip on each side (a parallelepiped sheared along x by the
-// trailing edge angle).  Each face is a grid of about panel x panel parallelograms, each split
-// along its diagonal from its first corner into two triangles, wound outward.  area: the
-// triangles' areas (nm^2).
-constexpr double kShieldDepth = 30.0, kShieldMargin = 40.0;
+// trailing edge angle); each side block (with a side shield gap) has its inner face parallel to
+// the pole's flared side at that gap, runs down-track from kSideLead behind the leading edge to
+// kSideClear short of the trailing block, and reaches out to the trailing block's cross-track
+// extent (a parallelepiped sheared along y by the side edge angle).  The blocks form one body.
+// Each face is a grid of about panel x panel parallelograms, each split along its diagonal from
+// its first corner into two triangles, wound outward.  area: the triangles' areas (nm^2).
+constexpr double kShieldDepth = 30.0, kShieldMargin = 40.0, kSideLead = 10.0, kSideClear = 0.5;
+
+struct Block {
+    V3 O, ex, ey, ez;
+};
 
 void shield_panels(const bpm_pole_geometry& g, double panel, std::vector<HeadTri>& P, std::vector<double>& area) {
     const double deg = kPi / 180.0;
-    const double tt = std::tan(g.trailing_edge_angle_deg * deg);
-    const double W = g.pole_tip_width_nm + 2.0 * kShieldMargin, T = g.shield_thickness_nm;
-    const V3 O{g.trailing_shield_gap_nm, -0.5 * W, g.z_abs_nm};
-    const V3 ex{kShieldDepth, 0, 0}, ey{0, W, 0}, ez{T * tt, 0, T};
-    const V3 C = vadd(O, vscale(0.5, vadd(vadd(ex, ey), ez)));
-    const V3 faces[6][3] = {{O, ex, ey},          {vadd(O, ez), ex, ey}, {O, ey, ez},
-                            {vadd(O, ex), ey, ez}, {O, ex, ez},          {vadd(O, ey), ex, ez}};
+    const double tt = std::tan(g.trailing_edge_angle_deg * deg), ts = std::tan(g.side_edge_angle_deg * deg);
+    const double w = g.pole_tip_width_nm, W = w + 2.0 * kShieldMargin, T = g.shield_thickness_nm;
+    std::vector<Block> blocks;
+    if (g.trailing_shield_gap_nm > 0.f)
+        blocks.push_back(Block{V3{g.trailing_shield_gap_nm, -0.5 * W, g.z_abs_nm}, V3{kShieldDepth, 0, 0},
+                               V3{0, W, 0}, V3{T * tt, 0, T}});
+    if (g.side_shield_gap_nm > 0.f) {
+        const double x0 = -g.abs_thickness_nm - kSideLead;
+        const double x1 = std::max(0.0, (double)g.trailing_shield_gap_nm) - kSideClear;
+        const double inner = 0.5 * w + g.side_shield_gap_nm, reach = 0.5 * W - inner;
+        blocks.push_back(Block{V3{x0, inner, g.z_abs_nm}, V3{x1 - x0, 0, 0}, V3{0, reach, 0}, V3{0, T * ts, T}});
+        blocks.push_back(Block{V3{x0, -0.5 * W, g.z_abs_nm}, V3{x1 - x0, 0, 0}, V3{0, reach, 0},
+                               V3{0, -T * ts, T}});
+    }
     P.clear();
     area.clear();
-    for (const auto& f : faces) {
-        const V3 F0 = f[0], U = f[1], V = f[2];
-        const int nu = std::max(1, (int)std::ceil(std::sqrt(vdot(U, U)) / panel - 1e-9));
-        const int nv = std::max(1, (int)std::ceil(std::sqrt(vdot(V, V)) / panel - 1e-9));
-        for (int i = 0; i < nu; ++i)
-            for (int j = 0; j < nv; ++j) {
-                auto pt = [&](int a, int b) {
-                    return vadd(F0, vadd(vscale((double)a / nu, U), vscale((double)b / nv, V)));
-                };
-                const V3 p00 = pt(i, j), p10 = pt(i + 1, j), p11 = pt(i + 1, j + 1), p01 = pt(i, j + 1);
-                const V3 tri[2][3] = {{p00, p10, p11}, {p00, p11, p01}};
-                for (const auto& t : tri) {
-                    V3 a = t[0], b = t[1], c = t[2];
-                    V3 nn = vcross(vsub(b, a), vsub(c, a));
-                    const V3 mid = vscale(1.0 / 3.0, vadd(vadd(a, b), c));
-                    if (vdot(nn, vsub(mid, C)) < 0) std::swap(b, c);
-                    HeadTri h{};
-                    set_tri(h, a, b, c, 0.0);
-                    P.push_back(h);
-                    area.push_back(0.5 * std::sqrt(vdot(nn, nn)));
+    for (const Block& bk : blocks) {
+        const V3 O = bk.O, ex = bk.ex, ey = bk.ey, ez = bk.ez;
+        const V3 C = vadd(O, vscale(0.5, vadd(vadd(ex, ey), ez)));
+        const V3 faces[6][3] = {{O, ex, ey},          {vadd(O, ez), ex, ey}, {O, ey, ez},
+                                {vadd(O, ex), ey, ez}, {O, ex, ez},          {vadd(O, ey), ex, ez}};
+        for (const auto& f : faces) {
+            const V3 F0 = f[0], U = f[1], V = f[2];
+            const int nu = std::max(1, (int)std::ceil(std::sqrt(vdot(U, U)) / panel - 1e-9));
+            const int nv = std::max(1, (int)std::ceil(std::sqrt(vdot(V, V)) / panel - 1e-9));
+            for (int i = 0; i < nu; ++i)
+                for (int j = 0; j < nv; ++j) {
+                    auto pt = [&](int a, int b) {
+                        return vadd(F0, vadd(vscale((double)a / nu, U), vscale((double)b / nv, V)));
+                    };
+                    const V3 p00 = pt(i, j), p10 = pt(i + 1, j), p11 = pt(i + 1, j + 1), p01 = pt(i, j + 1);
+                    const V3 tri[2][3] = {{p00, p10, p11}, {p00, p11, p01}};
+                    for (const auto& t : tri) {
+                        V3 a = t[0], b = t[1], c = t[2];
+                        V3 nn = vcross(vsub(b, a), vsub(c, a));
+                        const V3 mid = vscale(1.0 / 3.0, vadd(vadd(a, b), c));
+                        if (vdot(nn, vsub(mid, C)) < 0) std::swap(b, c);
+                        HeadTri h{};
+                        set_tri(h, a, b, c, 0.0);
+                        P.push_back(h);
+                        area.push_back(0.5 * std::sqrt(vdot(nn, nn)));
+                    }
                 }
-            }
+        }
     }
 }
 
@@ -472,10 +493,11 @@ extern "C" int bpm_head_field_solve(bpm_ctx* ctx, const bpm_pole_geometry* g, in
         set_error("the head-field grid must lie below the ABS (and above the under-layer)");
         return BPM_ERR_ARG;
     }
-    const bool shield = G.trailing_shield_gap_nm > 0.f;
+    const bool shield = G.trailing_shield_gap_nm > 0.f || G.side_shield_gap_nm > 0.f;
     const double panel = G.shield_panel_nm > 0.f ? G.shield_panel_nm : 2.0;
-    if (shield && (!(G.shield_thickness_nm > 0.f) || panel < 0.5)) {
-        set_error("a trailing shield needs a positive thickness and panels of at least 0.5 nm");
+    if (shield && (!(G.shield_thickness_nm > 0.f) || panel < 0.5 || !(G.side_shield_gap_nm < kShieldMargin))) {
+        set_error("a shield needs a positive thickness, panels of at least 0.5 nm and a side gap below %g nm",
+                  kShieldMargin);
         return BPM_ERR_ARG;
     }
     HeadTris pole{};

@@ -33,7 +33,8 @@ Readings (where the paper gives no number):
   the trailing edge, under the track's centre, at the islands' mid-height;
 * a rate above 1 (an Arrhenius rate with a vanishing barrier, or the sum of
   the three) is taken as 1, a probability;
-* the side shield gap has no effect (side shields are not modelled).
+* the shield is the wrap-around body of bpm_head_field_solve: trailing and side
+  blocks at Table I's gaps, Table I's thickness as their height.
 """
 from __future__ import annotations
 
@@ -87,7 +88,8 @@ def pole_geometry(p: dict, panel_nm: float = 3.0) -> dict:
                                taper_angle_deg=p["pole_tip_taper_angle_deg"],
                                z_abs_nm=Z_ABS_NM, z_sul_nm=Z_SUL_NM, sul_image=1,
                                trailing_shield_gap_nm=p["trailing_shield_gap_nm"],
-                               shield_thickness_nm=p["shield_thickness_nm"], shield_panel_nm=panel_nm)
+                               shield_thickness_nm=p["shield_thickness_nm"], shield_panel_nm=panel_nm,
+                               side_shield_gap_nm=p["side_shield_gap_nm"])
 
 
 def media(p: dict):

@@ -300,12 +300,12 @@ def pole_geometry(**overrides) -> dict:
     taper 75 deg), the yoke edge 153 nm above the ABS, CoFe at 2.4 T (Table II), a 20 nm deep
     ABS footprint, and the frame of synthetic_head_map: island tops at z = 10 nm, the ABS 6 nm
     above them (the paper's head-media spacing), the soft under-layer 20 nm below the ABS.  No
-    trailing shield unless trailing_shield_gap_nm is given (Table I's initial design: 9 nm gap,
-    10 nm thickness)."""
+    shields unless their gaps are given (Table I's initial design: trailing gap 9 nm, side gap
+    16 nm, thickness 10 nm)."""
     g = dict(pole_tip_width_nm=14.0, trailing_edge_angle_deg=20.0, side_edge_angle_deg=15.0,
              taper_angle_deg=75.0, abs_thickness_nm=20.0, yoke_edge_nm=153.0, Js_T=2.4,
              z_abs_nm=16.0, z_sul_nm=-4.0, sul_image=1, trailing_shield_gap_nm=0.0, shield_thickness_nm=0.0,
-             shield_panel_nm=2.0)
+             shield_panel_nm=2.0, side_shield_gap_nm=0.0)
     g.update(overrides)
     return g
 

@@ -112,6 +112,22 @@ def test_trailing_shield_field_matches_oracle(ctx):
     assert abs(want[-4, 2] - bare[-4, 2]) < 0.1 * abs(bare[-4, 2])
 
 
+def test_wrap_around_shield_matches_oracle(ctx):
+    # trailing and side shields as one equipotential body, against the oracle's solve
+    g = dict(SHIELDED, side_shield_gap_nm=16.0)
+    nx, ny, nz, h, org = 48, 40, 16, 1.0, (-36.0, -20.0, 0.0)
+    hm = ctx.head_field(g, nx, ny, nz, h, org)
+    rng = np.random.default_rng(6)
+    idx = np.stack([rng.integers(0, nx, 16), rng.integers(0, ny, 16), rng.integers(0, nz, 16)], 1)
+    idx = np.concatenate([idx, [[38, 32, 15], [30, 38, 12]]])
+    pts = np.asarray(org) + h * idx
+    want = polefield.field_with_shield(g, pts)
+    got = hm.B_T[idx[:, 2], idx[:, 1], idx[:, 0]].astype(np.float64)
+    err = float(np.abs(got - want).max())
+    print(f"wrap-around shield: max |B| {np.abs(want).max():.3f} T, max |dB| {err:.2e} T")
+    assert err <= 1e-6
+
+
 def test_trailing_shield_at_default_panels(ctx):
     # the default 2 nm panels (over four thousand unknowns): the solve passes its residual check
     # and converges to the 6 nm panels' field within the discretisation error

@@ -28,6 +28,7 @@ def test_table1_and_media_readings():
     g = model.pole_geometry(p)
     assert g["z_abs_nm"] == 18.0 and g["z_sul_nm"] < 0.0                     # 6 nm above the island tops
     assert g["trailing_shield_gap_nm"] == 9.0 and g["shield_thickness_nm"] == 10.0
+    assert g["side_shield_gap_nm"] == 16.0
 
 
 def test_write_window_and_bit_positions():

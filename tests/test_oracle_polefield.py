@@ -206,3 +206,32 @@ def test_shield_interior_is_at_the_shield_potential():
         assert abs(pp + shield_phi - Phi) <= 2e-3 * abs(Phi), (pp + shield_phi, Phi)
     # the pole drives the shield: its potential is not the under-layer's (zero)
     assert abs(Phi) > 0.1
+
+
+def test_side_shields_join_the_equipotential_body():
+    # trailing and side blocks form one body: the potential is the same constant inside each
+    # block; its charges sum to zero; the side shields pull the fringing field at the adjacent
+    # track (one cross-track pitch from the pole's centre, past the trailing edge)
+    g = synth.pole_geometry(trailing_shield_gap_nm=9.0, side_shield_gap_nm=16.0, shield_thickness_nm=10.0,
+                            shield_panel_nm=4.0)
+    blocks = polefield.shield_blocks(g)
+    assert len(blocks) == 3
+    tris, q, Phi = polefield.shield_charges(g)
+    areas = polefield.shield_panels(g)[1]
+    assert abs((q * areas).sum()) <= 1e-9 * np.abs(q * areas).sum()
+    img = tris.copy()
+    img[..., 2] = 2 * g["z_sul_nm"] - img[..., 2]
+    img = img[:, [0, 2, 1]]
+    inner = [corner + 0.5 * (dx + dy + dz) for corner, dx, dy, dz in blocks]
+    pole_phi = polefield.pole_potential(g, np.array(inner))
+    for P, pp in zip(inner, pole_phi):
+        v = pp + ((polefield.potential_closed(tris, P) - polefield.potential_closed(img, P)) * q).sum() / (4 * math.pi)
+        assert abs(v - Phi) <= 3e-3 * abs(Phi), (P, v, Phi)
+    # the side blocks clear the pole: inner faces the side gap outside the pole's flared sides
+    corner, dx, dy, dz = blocks[1]
+    assert corner[1] == pytest.approx(g["pole_tip_width_nm"] / 2 + 16.0)
+    assert dz[1] / dz[2] == pytest.approx(math.tan(math.radians(g["side_edge_angle_deg"])))
+    adj = np.array([[2.0, 11.7, 9.0]])
+    with_sides = polefield.field_with_shield(g, adj)[0]
+    trailing_only = polefield.field_with_shield(dict(g, side_shield_gap_nm=0.0), adj)[0]
+    assert abs(with_sides[2]) < abs(trailing_only[2])
