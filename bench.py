@@ -410,6 +410,17 @@ def measure_head_field(ctx, nx=64, ny=64, nz=18, reps=20):
                              "sample": f"{len(pts)} voxels, adaptive Gauss-Legendre quadrature of the same charges"}}
 
 
+def measure_model_evaluation(ctx):
+    """One model evaluation of Fig. 4 for Table I's initial design (staggered layout): head field
+    solved with its wrap-around shield, critical-field searches, NEB, BER_tot; wall-clock."""
+    from paper_1603_09493_gb300 import model
+    t = time.perf_counter()
+    r = model.evaluate(ctx, model.initial_design())
+    r["wall_s"] = time.perf_counter() - t
+    r["design"] = "Table I initial design"
+    return r
+
+
 def measure_ego(ctx, n=240, d=12, T=256, N=1 << 20):
     """EGO steps on the GPU (Sec. II.A) at the paper's scale of ten or more training
     designs per parameter: a batch of T likelihood evaluations (one Cholesky each)
@@ -903,6 +914,7 @@ def main(args):
                                     mats=None if args.no_cpu else mats)
         extras["ego"] = measure_ego(ctx)
         extras["head_field"] = measure_head_field(ctx)
+        extras["model_evaluation"] = measure_model_evaluation(ctx)
         extras["search"] = measure_search(ctx)
     ctx.close()
     if rank != 0:
