@@ -168,12 +168,22 @@ int bpm_mesh_info_get(bpm_ctx* ctx, int32_t mesh_id, bpm_mesh_info* out);
  * documented at the BPM_OP_* constant. */
 int bpm_mesh_get_operator(bpm_ctx* ctx, int32_t mesh_id, int32_t which, void* dst);
 
+/* Release a mesh's device operators and buffers; its id then names no mesh.
+ * Waits for the context stream.  BPM_ERR_ARG for an unknown id,
+ * BPM_ERR_STATE while a live batch integrates islands of the mesh. */
+int bpm_mesh_release(bpm_ctx* ctx, int32_t mesh_id);
+
 /* Upload a head-field map mu0*H [nz][ny][nx][3] (host, float32).  Voxel
  * (ix,iy,iz) sits at origin + h*(ix,iy,iz); x is in the head frame, y and z
  * in the media frame.  Lookups are trilinear, clamped to the grid box.
  * nx, ny, nz >= 2. */
 int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, int32_t nz,
                        float h_nm, const float origin_nm[3], int32_t* map_id_out);
+
+/* Release a head map (its voxels, array and texture); its id then names no
+ * map.  Waits for the context stream.  BPM_ERR_ARG for an unknown id,
+ * BPM_ERR_STATE while a live batch uses the map. */
+int bpm_headmap_release(bpm_ctx* ctx, int32_t map_id);
 
 /* ---------------------------------------------------------------------- */
 /* Head field of a saturated main pole (Sec. II.A head model, Table I)     */

@@ -98,6 +98,8 @@ PROTOTYPES = {
     "bpm_mesh_get_operator": (c_int, [c_void_p, c_int32, c_int32, c_void_p]),
     "bpm_head_field_solve": (c_int, [c_void_p, POINTER(bpm_pole_geometry), c_int32, c_int32, c_int32, c_float,
                                      c_void_p, c_void_p, c_int]),
+    "bpm_mesh_release": (c_int, [c_void_p, c_int32]),
+    "bpm_headmap_release": (c_int, [c_void_p, c_int32]),
     "bpm_headmap_upload": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p,
                                    POINTER(c_int32)]),
     "bpm_batch_create": (c_int, [c_void_p, c_void_p, c_int32, POINTER(bpm_run_params), POINTER(c_void_p)]),

@@ -132,6 +132,14 @@ class Context:
         L.check(self.lib.bpm_mesh_get_operator(self.h, mesh_id, which, L.ptr(out)))
         return out
 
+    def mesh_release(self, mesh_id: int):
+        """Free a mesh's device operators (bpm_mesh_release); no live batch may use it."""
+        L.check(self.lib.bpm_mesh_release(self.h, int(mesh_id)))
+
+    def headmap_release(self, map_id: int):
+        """Free a head map (bpm_headmap_release); no live batch may use it."""
+        L.check(self.lib.bpm_headmap_release(self.h, int(map_id)))
+
     def headmap_upload(self, hm) -> int:
         B = np.ascontiguousarray(hm.B_T, np.float32)
         nz, ny, nx = B.shape[:3]

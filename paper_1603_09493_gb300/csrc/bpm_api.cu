@@ -714,6 +714,43 @@ int bpm_mesh_get_operator(bpm_ctx* ctx, int32_t mesh_id, int32_t which, void* ds
     }
 }
 
+int bpm_mesh_release(bpm_ctx* ctx, int32_t mesh_id) {
+    Mesh* M = get_mesh(ctx, mesh_id);
+    if (!M) return BPM_ERR_ARG;
+    for (const bpm_batch* b : live_batches(ctx))
+        for (const auto& g : b->groups)
+            if (g.mesh == M) {
+                set_error("mesh %d is used by a live batch", mesh_id);
+                return BPM_ERR_STATE;
+            }
+    BPM_TRY(ensure_device(ctx));
+    BPM_CK(cudaStreamSynchronize(ctx->stream));   // work queued on the mesh's buffers finishes first
+    free_mesh(M);
+    ctx->meshes[mesh_id] = nullptr;
+    return BPM_OK;
+}
+
+int bpm_headmap_release(bpm_ctx* ctx, int32_t map_id) {
+    if (!ctx || map_id < 0 || map_id >= (int)ctx->maps.size() || !ctx->maps[map_id]) {
+        set_error("unknown head map id %d", map_id);
+        return BPM_ERR_ARG;
+    }
+    HeadMap* H = ctx->maps[map_id];
+    for (const bpm_batch* b : live_batches(ctx))
+        if (b->map == H) {
+            set_error("head map %d is used by a live batch", map_id);
+            return BPM_ERR_STATE;
+        }
+    BPM_TRY(ensure_device(ctx));
+    BPM_CK(cudaStreamSynchronize(ctx->stream));
+    if (H->tex) cudaDestroyTextureObject(H->tex);
+    if (H->arr) cudaFreeArray(H->arr);
+    cudaFree(H->B);
+    delete H;
+    ctx->maps[map_id] = nullptr;
+    return BPM_OK;
+}
+
 int bpm_headmap_upload(bpm_ctx* ctx, const float* B_T, int32_t nx, int32_t ny, int32_t nz, float h_nm,
                        const float origin_nm[3], int32_t* map_id_out) {
     if (!ctx || !B_T || !origin_nm || !map_id_out || nx < 2 || ny < 2 || nz < 2 || !(h_nm > 0)) {
@@ -790,7 +827,7 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
     BPM_TRY(run_substeps(ctx, isl, B, p, &k_steps));
     HeadMap* H = nullptr;
     if (p->map_id >= 0) {
-        if (p->map_id >= (int)ctx->maps.size()) {
+        if (p->map_id >= (int)ctx->maps.size() || !ctx->maps[p->map_id]) {
             set_error("unknown head map id %d", p->map_id);
             return BPM_ERR_ARG;
         }

@@ -75,7 +75,7 @@ extern "C" int bpm_neb_run(bpm_ctx* ctx, const bpm_island* isl, int32_t D, const
     }
     const HeadMap* H = nullptr;
     if (p->map_id >= 0) {
-        if (p->map_id >= (int)ctx->maps.size()) {
+        if (p->map_id >= (int)ctx->maps.size() || !ctx->maps[p->map_id]) {
             set_error("unknown head map id %d", p->map_id);
             return BPM_ERR_ARG;
         }

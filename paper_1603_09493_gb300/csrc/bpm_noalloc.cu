@@ -85,7 +85,7 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
     BPM_TRY(run_substeps(ctx, isl, B, p, &k_steps));
     const HeadMap* H = nullptr;
     if (p->map_id >= 0) {
-        if (p->map_id >= (int)ctx->maps.size()) {
+        if (p->map_id >= (int)ctx->maps.size() || !ctx->maps[p->map_id]) {
             set_error("unknown head map id %d", p->map_id);
             return BPM_ERR_ARG;
         }

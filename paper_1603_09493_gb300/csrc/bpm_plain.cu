@@ -252,7 +252,7 @@ extern "C" int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, con
     BPM_TRY(run_substeps(ctx, isl, B, p, &k_steps));
     const HeadMap* H = nullptr;
     if (p->map_id >= 0) {
-        if (p->map_id >= (int)ctx->maps.size()) {
+        if (p->map_id >= (int)ctx->maps.size() || !ctx->maps[p->map_id]) {
             set_error("unknown head map id %d", p->map_id);
             return BPM_ERR_ARG;
         }
@@ -406,7 +406,7 @@ extern "C" int bpm_run_plain_f64(bpm_ctx* ctx, const bpm_island* isl, int32_t B,
     BPM_TRY(run_substeps(ctx, isl, B, p, &k_steps));
     const HeadMap* H = nullptr;
     if (p->map_id >= 0) {
-        if (p->map_id >= (int)ctx->maps.size()) {
+        if (p->map_id >= (int)ctx->maps.size() || !ctx->maps[p->map_id]) {
             set_error("unknown head map id %d", p->map_id);
             return BPM_ERR_ARG;
         }

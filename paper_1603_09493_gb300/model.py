@@ -174,6 +174,8 @@ def evaluate(ctx, p: dict, layout: str = "staggered", precision: int = L.PREC_BF
                    E_B_kT=float(bar["E_B_kT"][0]), ber_adj=min(1.0, float(bar["ber_adj"][0])),
                    llg_island_runs=int(targ.n_runs + prev.n_runs))
         out["ber_tot"] = min(1.0, float(adjacent.ber_tot(out["ber_targ"], out["ber_prev"], out["ber_adj"])))
+    ctx.mesh_release(mid)              # a loop uploads one mesh and one map per design
+    ctx.headmap_release(hid)
     stamps = list(t.items())
     out["seconds"] = {k: stamps[i][1] - stamps[i - 1][1] for i, (k, _) in enumerate(stamps) if i > 0}
     return out

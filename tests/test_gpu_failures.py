@@ -113,3 +113,36 @@ def test_a_real_gemm_wait_runs_out_and_the_batch_recovers(ctx, mid):
     assert np.all(out["status"] == 0)
     with pytest.raises(L.BpmError):
         L.check(ctx.lib.bpm_debug_set_gemm_wait(None, 5.0))
+
+
+def test_meshes_and_maps_are_released(ctx):
+    # a released mesh or map is gone: runs naming it are refused; release is refused while a
+    # live batch uses it, and a second release is refused
+    mesh, mats = synth.small_island_mesh(), synth.ecc_materials()
+    mid = ctx.mesh_upload(mesh, mats)
+    hid = ctx.headmap_upload(synth.synthetic_head_map())
+    isl = synth.jittered_islands(4, seed=2, mesh_id=mid)
+    p = synth.RunParams(dt_ps=0.1, substeps=4, alpha=0.1, use_map=True)
+    with ctx.batch(isl, p, precision=L.PREC_BF16X3, map_id=hid) as bt:
+        for fn, i in ((ctx.mesh_release, mid), (ctx.headmap_release, hid)):
+            with pytest.raises(L.BpmError) as e:
+                fn(i)
+            assert e.value.code == L.BPM_ERR_STATE
+        bt.advance(1)
+    ctx.headmap_release(hid)
+    with pytest.raises(L.BpmError) as e:
+        ctx.run_batch(isl, p, 1, map_id=hid)
+    assert e.value.code == L.BPM_ERR_ARG
+    ctx.mesh_release(mid)
+    with pytest.raises(L.BpmError) as e:
+        ctx.run_batch(isl, synth.RunParams(dt_ps=0.1, substeps=4, alpha=0.1), 1)
+    assert e.value.code == L.BPM_ERR_ARG
+    for fn, i in ((ctx.mesh_release, mid), (ctx.headmap_release, hid)):
+        with pytest.raises(L.BpmError) as e:
+            fn(i)
+        assert e.value.code == L.BPM_ERR_ARG
+    # the context still works: a new mesh gets a new id and runs
+    mid2 = ctx.mesh_upload(mesh, mats)
+    assert mid2 != mid
+    out = ctx.run_batch(synth.jittered_islands(2, seed=3, mesh_id=mid2), synth.RunParams(dt_ps=0.1, substeps=4), 1)
+    assert np.all(out["status"] == 0)

@@ -67,6 +67,12 @@ class _FakeCtx:
     def mesh_upload(self, mesh, mats):
         return 0
 
+    def mesh_release(self, mid):
+        pass
+
+    def headmap_release(self, hid):
+        pass
+
 
 def test_evaluation_flow(monkeypatch):
     # stand-ins: the target switches unless H_ext opposes the head by more than 2.3 sigma, the
