@@ -130,9 +130,10 @@ def gemm_traffic(prec, B, n):
 
 
 # Warp instructions per island-node of the Heun stage kernels (two islands per CTA, BF16x3
-# operand) from ncu's smsp__inst_executed.sum of one launch over 2048 islands of the 1547-node
-# mesh (profiles/heun_stages_census_2048.md: 50.7 M and 52.5 M).  Remove when the kernels change.
-NCU_STAGE_WARP_INSTR = {1547: (50.7e6 / (2048 * 1547), 52.5e6 / (2048 * 1547))}
+# operand) from ncu's smsp__inst_executed.sum of one launch over the 1024 islands of one chain
+# (2048 islands, two chains) of the 1547-node mesh (profiles/heun_stages_census_2048.md: 24.30 M
+# and 26.87 M).  Remove when the kernels change.
+NCU_STAGE_WARP_INSTR = {1547: (24.30e6 / (1024 * 1547), 26.87e6 / (1024 * 1547))}
 SM_COUNT = 152
 ISSUE_PER_SM_CLK = 4           # one warp instruction per scheduler per cycle, four schedulers per SM
 
@@ -857,11 +858,13 @@ def main(args):
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = gemm_traffic(prec, B, n)
     roof["kernel"] = "demag GEMM"
-    # step kernels: algorithmic HBM bytes (stage 1: 60 n, stage 2: 72 n per island)
+    # step kernels: algorithmic HBM bytes, 48 n (stage 1) and 60 n (stage 2) per island. Stage 1
+    # reads m and B_d and writes k1 and the operand; stage 2 reads m, k1 and B_d and writes m and
+    # the operand (m* is rebuilt from m and k1, not stored). The operand is 12 B a node: FP32, or
+    # BF16 hi plus lo.
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
-    ab = 2 if prec != L.PREC_FP32 else 1
-    s1_bytes = B * n * (12 + 12 + 12 + 12 + 6 * ab)
-    s2_bytes = B * n * (12 * 4 + 12 + 6 * ab)
+    s1_bytes = B * n * (12 + 12 + 12 + 12)
+    s2_bytes = B * n * (12 * 3 + 12 + 12)
     roof_steps = {"bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
                   "stage1_achieved": s1_bytes / (kt["stage1_ms"] * 1e-3) / 1e9,
                   "stage2_achieved": s2_bytes / (kt["stage2_ms"] * 1e-3) / 1e9}

@@ -515,8 +515,8 @@ int bpm_surrogate_destroy(bpm_ctx* ctx, int32_t sid);
  *   m           device [B][3][ld]: the state at p->t0_ps on entry, the state
  *               after n_intervals intervals on return (stream-ordered)
  *   mz          device [B] volume-averaged m_z at the end, or NULL
- * Requests whose scratch would exceed the array (about 60*B*n_pad bytes, e.g.
- * 80 islands of a 1547-node mesh) fail with BPM_ERR_ARG and a message giving
+ * Requests whose scratch would exceed the array (about 48*B*n_pad bytes, e.g.
+ * 111 islands of a 1547-node mesh) fail with BPM_ERR_ARG and a message giving
  * the size needed.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress).  All calls share the one array, which keeps
  * the previous call's contents (each call clears the region it uses): calls

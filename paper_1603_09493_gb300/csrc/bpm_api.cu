@@ -113,7 +113,7 @@ struct Group {
     std::vector<int> user_idx;    // batch island index of each group row
     int* d_idx = nullptr;
     float4* isl = nullptr;
-    float *m = nullptr, *ms = nullptr, *k1 = nullptr, *Hd = nullptr, *A32 = nullptr;
+    float *m = nullptr, *k1 = nullptr, *Hd = nullptr, *A32 = nullptr;
     __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr;
     float *mz_prev = nullptr, *t_sw = nullptr;
     int *crossed = nullptr, *status = nullptr;
@@ -255,7 +255,6 @@ int setup_chains(bpm_batch* bt) {
         a.B = std::min(chunk, g.B - b0);
         a.isl += 3 * (size_t)b0;
         a.m += S;
-        a.ms += S;
         a.k1 += S;
         a.Hd += off;
         if (a.A32) a.A32 += off;
@@ -432,7 +431,7 @@ int enqueue_interval(bpm_batch* bt, cudaStream_t s) {
 }
 
 void free_group(Group& g) {
-    void* ptrs[] = {g.d_idx, g.isl, g.m, g.ms, g.k1, g.Hd, g.A32, g.Ahi, g.Alo, g.mz_prev, g.t_sw, g.crossed, g.status};
+    void* ptrs[] = {g.d_idx, g.isl, g.m, g.k1, g.Hd, g.A32, g.Ahi, g.Alo, g.mz_prev, g.t_sw, g.crossed, g.status};
     for (void* p : ptrs) cudaFree(p);
 }
 
@@ -878,7 +877,6 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         chk(dalloc(&g.d_idx, g.B));
         chk(dalloc(&g.isl, 3 * (size_t)g.B));
         chk(dalloc(&g.m, S));
-        chk(dalloc(&g.ms, S));
         chk(dalloc(&g.k1, S));
         chk(dalloc(&g.Hd, S));
         if (p->precision == BPM_PREC_FP32) {
@@ -928,7 +926,6 @@ int bpm_batch_create(bpm_ctx* ctx, const bpm_island* isl, int32_t B, const bpm_r
         a.moy = H ? H->origin[1] : 0.f;
         a.moz = H ? H->origin[2] : 0.f;
         a.m = g.m;
-        a.ms = g.ms;
         a.k1 = g.k1;
         a.Hd = g.Hd;
         a.A32 = g.A32;

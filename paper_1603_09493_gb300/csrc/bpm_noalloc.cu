@@ -104,8 +104,6 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
     off = align256(off + 3 * (size_t)B * sizeof(float4));
     const size_t o_m = off;
     off = align256(off + state);
-    const size_t o_ms = off;
-    off = align256(off + state);
     const size_t o_k1 = off;
     off = align256(off + state);
     const size_t o_hd = off;
@@ -171,7 +169,6 @@ extern "C" int bpm_llg_advance_noalloc(bpm_ctx* ctx, const bpm_island* isl, int3
     a.moy = H ? H->origin[1] : 0.f;
     a.moz = H ? H->origin[2] : 0.f;
     a.m = m_in;
-    a.ms = reinterpret_cast<float*>(s8 + o_ms);
     a.k1 = reinterpret_cast<float*>(s8 + o_k1);
     float* hd = reinterpret_cast<float*>(s8 + o_hd);
     a.Hd = hd;

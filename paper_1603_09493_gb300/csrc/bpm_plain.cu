@@ -283,7 +283,7 @@ extern "C" int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, con
     int *iscal = nullptr;
     long long* interval = nullptr;
     float4* d_isl = nullptr;
-    BPM_CK(cudaMalloc(&buf, 5 * S * sizeof(float)));
+    BPM_CK(cudaMalloc(&buf, 4 * S * sizeof(float)));
     BPM_CK(cudaMalloc(&scal, 2 * sizeof(float)));
     BPM_CK(cudaMalloc(&iscal, 2 * sizeof(int)));
     BPM_CK(cudaMalloc(&interval, sizeof(long long)));
@@ -301,7 +301,7 @@ extern "C" int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, con
                         make_float4(I.u[0], I.u[1], I.u[2], I.pos_nm[0]),
                         make_float4(I.pos_nm[1], I.Hext_T[0], I.Hext_T[1], I.Hext_T[2])};
         cudaMemcpyAsync(d_isl, ip, sizeof(ip), cudaMemcpyHostToDevice, s);
-        cudaMemsetAsync(buf, 0, 5 * S * sizeof(float), s);
+        cudaMemsetAsync(buf, 0, 4 * S * sizeof(float), s);
         cudaMemsetAsync(interval, 0, sizeof(long long), s);
         StepArgs a{};
         a.B = 1;
@@ -324,11 +324,10 @@ extern "C" int bpm_run_plain(bpm_ctx* ctx, const bpm_island* isl, int32_t B, con
         a.moy = H ? H->origin[1] : 0.f;
         a.moz = H ? H->origin[2] : 0.f;
         a.m = buf;
-        a.ms = buf + S;
-        a.k1 = buf + 2 * S;
-        float* hd = buf + 3 * S;
+        a.k1 = buf + S;
+        float* hd = buf + 2 * S;
         a.Hd = hd;
-        a.A32 = buf + 4 * S;
+        a.A32 = buf + 3 * S;
         a.prec = BPM_PREC_FP32;
         a.mz_prev = scal;
         a.t_sw = scal + 1;

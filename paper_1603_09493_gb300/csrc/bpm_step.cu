@@ -8,14 +8,18 @@
 // m_{n+1} = N(m_n + h/2 (k1 + k2)), N(v) = v/|v|.
 //
 // Stage 1 (predictor) and stage 2 (corrector) each stage the island's source
-// state in shared memory (component-planar, as in global memory) for the
-// exchange gather, evaluate the local field terms (the head map is read through
-// L1: staging the island's map window in shared memory was measured slower,
-// because the extra shared memory costs occupancy), take the Heun stage,
-// renormalise, and write the demag GEMM operand of the new state (Ms * m, FP32
-// or BF16 hi/lo).  Stage 2 also updates the volume-averaged
-// <m_z> switch detector with a fixed-order block reduction.  The demag field of
-// the stage's source state comes from the GEMM that ran just before the stage.
+// state in shared memory for the exchange gather, evaluate the local field terms
+// (the head map is read through L1: staging the island's map window in shared
+// memory was measured slower, because the extra shared memory costs occupancy),
+// take the Heun stage, renormalise, and write the demag GEMM operand of the new
+// state (Ms * m, FP32 or BF16 hi/lo).  The predictor state m* is not kept in
+// global memory: stage 1 writes k1 and the operand of m*, and stage 2 rebuilds
+// m* = N(m_n + h k1) from m_n and k1 while staging, with the same rounding as
+// stage 1 (heun_predict), so that both stages see the same m*.  Stage 2 also
+// updates the volume-averaged <m_z> switch detector with a fixed-order block
+// reduction.  The demag field of the stage's source state comes from the GEMM
+// that ran just before the stage.  Streaming loads (state, slopes, demag field)
+// are cached in L2 only, leaving L1 to the entry table and the head map.
 #include <algorithm>
 #include <cmath>
 
@@ -35,6 +39,27 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 __device__ __forceinline__ float3 normalize3(float3 v) {
     float r = rsqrtf(dot3(v, v));
     return r * v;
+}
+
+// Heun predictor N(m + h f), written out so that stage 1 and stage 2 round it alike
+__device__ __forceinline__ float3 heun_predict(float3 m, float3 f, float hf) {
+    const float x = __fmaf_rn(hf, f.x, m.x), y = __fmaf_rn(hf, f.y, m.y), z = __fmaf_rn(hf, f.z, m.z);
+    const float r = rsqrtf(__fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x))));
+    return f3(__fmul_rn(r, x), __fmul_rn(r, y), __fmul_rn(r, z));
+}
+
+// predictor state of nodes 4q .. 4q + 3 from four-node quads of m and k1 (zero beyond n)
+__device__ __forceinline__ void predict4(float4& x, float4& y, float4& z, float4 kx, float4 ky, float4 kz, float hf,
+                                         int j, int n) {
+    float3 v;
+    v = j < n ? heun_predict(f3(x.x, y.x, z.x), f3(kx.x, ky.x, kz.x), hf) : f3(0, 0, 0);
+    x.x = v.x; y.x = v.y; z.x = v.z;
+    v = j + 1 < n ? heun_predict(f3(x.y, y.y, z.y), f3(kx.y, ky.y, kz.y), hf) : f3(0, 0, 0);
+    x.y = v.x; y.y = v.y; z.y = v.z;
+    v = j + 2 < n ? heun_predict(f3(x.z, y.z, z.z), f3(kx.z, ky.z, kz.z), hf) : f3(0, 0, 0);
+    x.z = v.x; y.z = v.y; z.z = v.z;
+    v = j + 3 < n ? heun_predict(f3(x.w, y.w, z.w), f3(kx.w, ky.w, kz.w), hf) : f3(0, 0, 0);
+    x.w = v.x; y.w = v.y; z.w = v.z;
 }
 
 // continuous map coordinate of a point, clamped to the grid box
@@ -74,7 +99,7 @@ __device__ __forceinline__ float3 eff_field(const StepArgs& a, int b, int i, flo
     float3 hdv = f3(0, 0, 0);
     if (mask & BPM_TERM_DEMAG) {
         const float* hd = a.Hd + (size_t)b * a.kp + i;
-        hdv = f3(hd[0], hd[np], hd[2 * np]);
+        hdv = f3(__ldcg(hd), __ldcg(hd + np), __ldcg(hd + 2 * np));
     }
     const float4 pos = __ldg(a.node_pos + i);
     const float an0 = __ldg(&a.node_mat[i].x);
@@ -132,11 +157,26 @@ __device__ __forceinline__ void write_gemm_input(const StepArgs& a, int b, int i
     }
 }
 
+// predictor state of one island from its planar m and k1 -> planar shared state
+__device__ __forceinline__ void stage_predicted(const float* m, const float* k1, float* sm, int np, int n, float hf) {
+    const float4* m4 = reinterpret_cast<const float4*>(m);
+    const float4* k4 = reinterpret_cast<const float4*>(k1);
+    float4* d4 = reinterpret_cast<float4*>(sm);
+    const int nq = np / 4;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        float4 x = __ldcg(m4 + q), y = __ldcg(m4 + nq + q), z = __ldcg(m4 + 2 * nq + q);
+        predict4(x, y, z, __ldcg(k4 + q), __ldcg(k4 + nq + q), __ldcg(k4 + 2 * nq + q), hf, 4 * q, n);
+        d4[q] = x;
+        d4[nq + q] = y;
+        d4[2 * nq + q] = z;
+    }
+}
+
 // planar [3][n_pad] global state -> shared memory, 16-byte copies
 __device__ __forceinline__ void stage_state(const float* src, float* sm, int n_pad) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(sm);
-    for (int q = threadIdx.x; q < 3 * n_pad / 4; q += blockDim.x) d4[q] = s4[q];
+    for (int q = threadIdx.x; q < 3 * n_pad / 4; q += blockDim.x) d4[q] = __ldcg(s4 + q);
 }
 
 __device__ __forceinline__ float block_reduce(float v, float* red) {
@@ -171,13 +211,10 @@ __device__ __forceinline__ void stage1_body(const StepArgs& a, int b, int j) {
         float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
         float3 B = eff_field(a, b, i, mi, sm, p0, p1, p2, ramp, xh, a.mask);
         float3 f = llg_rhs(mi, B, a.alpha, a.gp);
-        float3 v = normalize3(mi + hf * f);
+        float3 v = heun_predict(mi, f, hf);
         a.k1[base + i] = f.x;
         a.k1[base + np + i] = f.y;
         a.k1[base + 2 * np + i] = f.z;
-        a.ms[base + i] = v.x;
-        a.ms[base + np + i] = v.y;
-        a.ms[base + 2 * np + i] = v.z;
         write_gemm_input(a, b, i, v, __ldg(&a.node_mat[i].y) * p0.z);
     }
 }
@@ -192,14 +229,14 @@ __device__ __forceinline__ void stage2_body(const StepArgs& a, int b, int j, flo
     const double t = step_time(a, j) + a.h;
     const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
     const float xh = a.x0 + a.v_nm_ps * (float)t;
-    stage_state(a.ms + base, sm, np);
+    stage_predicted(a.m + base, a.k1 + base, sm, np, a.n, (float)a.h);
     const float hh = 0.5f * (float)a.h;
     __syncthreads();
     float mzp = 0.f;
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         float3 mi = f3(sm[i], sm[np + i], sm[2 * np + i]);
-        const float3 mn = f3(a.m[base + i], a.m[base + np + i], a.m[base + 2 * np + i]);
-        const float3 f1 = f3(a.k1[base + i], a.k1[base + np + i], a.k1[base + 2 * np + i]);
+        const float3 mn = f3(__ldcg(a.m + base + i), __ldcg(a.m + base + np + i), __ldcg(a.m + base + 2 * np + i));
+        const float3 f1 = f3(__ldcg(a.k1 + base + i), __ldcg(a.k1 + base + np + i), __ldcg(a.k1 + base + 2 * np + i));
         float3 B = eff_field(a, b, i, mi, sm, p0, p1, p2, ramp, xh, a.mask);
         float3 f2 = llg_rhs(mi, B, a.alpha, a.gp);
         float3 v = normalize3(mn + hh * (f1 + f2));
@@ -274,7 +311,24 @@ __device__ __forceinline__ void stage_state_il(const float* src, float* sm, int 
         const int w = 4 * k;
         const int c = (w >= np) + (w >= 2 * np);
         const int j = w - c * np;
-        *reinterpret_cast<float4*>(sm + il_word(j) + 32 * (3 * q + c)) = s4[k];
+        *reinterpret_cast<float4*>(sm + il_word(j) + 32 * (3 * q + c)) = __ldcg(s4 + k);
+    }
+}
+
+// predictor states of islands b0 .. b0 + nb - 1 -> the interleaved shared state
+__device__ __forceinline__ void stage_predicted_il(const float* m, const float* k1, float* sm, int np, int n, int nb,
+                                                   float hf) {
+    const int nq = np / 4;
+    for (int t = threadIdx.x; t < nb * nq; t += blockDim.x) {
+        const int q = t / nq, qq = t - q * nq;
+        const float4* m4 = reinterpret_cast<const float4*>(m + (size_t)q * 3 * np);
+        const float4* k4 = reinterpret_cast<const float4*>(k1 + (size_t)q * 3 * np);
+        float4 x = __ldcg(m4 + qq), y = __ldcg(m4 + nq + qq), z = __ldcg(m4 + 2 * nq + qq);
+        predict4(x, y, z, __ldcg(k4 + qq), __ldcg(k4 + nq + qq), __ldcg(k4 + 2 * nq + qq), hf, 4 * qq, n);
+        float* d = sm + il_word(4 * qq) + 96 * q;
+        *reinterpret_cast<float4*>(d) = x;
+        *reinterpret_cast<float4*>(d + 32) = y;
+        *reinterpret_cast<float4*>(d + 64) = z;
     }
 }
 
@@ -332,7 +386,7 @@ __device__ __forceinline__ float3 field_from_sums(const StepArgs& a, float3 mi, 
 
 __device__ __forceinline__ float3 load_hd(const StepArgs& a, int b, int i) {
     const float* hd = a.Hd + (size_t)b * a.kp + i;
-    return f3(hd[0], hd[a.n_pad], hd[2 * a.n_pad]);
+    return f3(__ldcg(hd), __ldcg(hd + a.n_pad), __ldcg(hd + 2 * a.n_pad));
 }
 
 // predictor of islands b0 .. b0 + nb - 1 (nb <= IPB); sp: [IPB][3] island parameters in smem
@@ -369,13 +423,10 @@ __device__ __forceinline__ void stage1_multi(const StepArgs& a, int b0, int j, f
             const float4 p0 = sp[3 * q], p1 = sp[3 * q + 1], p2 = sp[3 * q + 2];
             float3 B = field_from_sums(a, mi[q], bex[q], hdv[q], p0, p1, p2, pos, nm.x, ramp, xh, mask);
             float3 f = llg_rhs(mi[q], B, a.alpha, a.gp);
-            float3 v = normalize3(mi[q] + hf * f);
+            float3 v = heun_predict(mi[q], f, hf);
             a.k1[base + i] = f.x;
             a.k1[base + np + i] = f.y;
             a.k1[base + 2 * np + i] = f.z;
-            a.ms[base + i] = v.x;
-            a.ms[base + np + i] = v.y;
-            a.ms[base + 2 * np + i] = v.z;
             write_gemm_input(a, b, i, v, nm.y * p0.z);
             }
         }
@@ -393,7 +444,7 @@ __device__ __forceinline__ void stage2_multi(const StepArgs& a, int b0, int j, f
     const double t = step_time(a, j) + a.h;
     const float ramp = a.rise > 0.f ? fminf(1.f, (float)(t / a.rise)) : 1.f;
     const float xh = a.x0 + a.v_nm_ps * (float)t;
-    for (int q = 0; q < nb; ++q) stage_state_il(a.ms + (size_t)(b0 + q) * S, sm, np, q);
+    stage_predicted_il(a.m + (size_t)b0 * S, a.k1 + (size_t)b0 * S, sm, np, a.n, nb, (float)a.h);
     const float hh = 0.5f * (float)a.h;
     const unsigned mask = a.mask;
     __syncthreads();
@@ -417,8 +468,8 @@ __device__ __forceinline__ void stage2_multi(const StepArgs& a, int b0, int j, f
             const int b = b0 + q;
             const size_t base = (size_t)b * S;
             const float4 p0 = sp[3 * q], p1 = sp[3 * q + 1], p2 = sp[3 * q + 2];
-            const float3 mn = f3(a.m[base + i], a.m[base + np + i], a.m[base + 2 * np + i]);
-            const float3 f1 = f3(a.k1[base + i], a.k1[base + np + i], a.k1[base + 2 * np + i]);
+            const float3 mn = f3(__ldcg(a.m + base + i), __ldcg(a.m + base + np + i), __ldcg(a.m + base + 2 * np + i));
+            const float3 f1 = f3(__ldcg(a.k1 + base + i), __ldcg(a.k1 + base + np + i), __ldcg(a.k1 + base + 2 * np + i));
             float3 B = field_from_sums(a, mi[q], bex[q], hdv[q], p0, p1, p2, pos, nm.x, ramp, xh, mask);
             float3 f2 = llg_rhs(mi[q], B, a.alpha, a.gp);
             float3 v = normalize3(mn + hh * (f1 + f2));

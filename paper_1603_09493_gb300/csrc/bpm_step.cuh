@@ -18,7 +18,6 @@ struct StepArgs {
     int mx, my, mz;
     float mh, mox, moy, moz;
     float* m;                 // [Bp][3][n_pad]
-    float* ms;                // predictor state m*
     float* k1;                // predictor slope
     const float* Hd;          // demag field of the GEMM input state, tesla, [Bp][kp]
     float* A32;               // GEMM input (FP32), [Bp][kp], Ms * m in MA/m (planes at c n_pad)
