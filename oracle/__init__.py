@@ -20,7 +20,11 @@ Modules
   neb       nudged elastic band for the adjacent-track barrier (Sec. II.C, Eq. 3)
   ego       efficient global optimisation: maximin Latin hypercube, kriging, EI (Sec. II.A)
 
-Parity status: the full switching dynamics of an island is pinned only
-through its invariants and closed-form special cases (no trajectory is printed
-in the paper) -- "parity unpinned" beyond those, see tests/test_oracle_*.py.
+Parity status: every module is pinned (tests/test_oracle_*.py).  The
+dynamics of a meshed island are pinned through closed-form special cases
+(macrospin precession, damped reversal, the Stoner-Wohlfarth astroid), the
+linear modes of a meshed two-layer island (an eigenproblem of its exchange and
+anisotropy operators) and invariants (|m| = 1, energy decay under damping).
+The large-angle switching of a meshed island has no closed form, and the paper
+prints no trajectory: it rests on those pins.
 """

@@ -1,7 +1,9 @@
 """Pins of the oracle's LLG integrator, fields and switch detector against
 closed forms: Larmor precession, the damped reversal time of a single spin in
-an antiparallel field, the Stoner-Wohlfarth astroid, trilinear exactness on
-affine fields, energy decay under damping, and |m| = 1."""
+an antiparallel field, the Stoner-Wohlfarth astroid, the linear modes of a
+meshed two-layer island (an eigenproblem of its exchange and anisotropy
+operators), trilinear exactness on affine fields, energy decay under damping,
+and |m| = 1."""
 import math
 
 import numpy as np
@@ -164,6 +166,55 @@ def test_energy_decays_and_norm_is_kept(small_ops):
     assert np.all(dE <= 1e-9 * np.abs(E[:-1])), dE.max()
     assert E[-1].max() < E[0].min()
     assert max(norms) < 1e-14
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.1])
+def test_linear_modes_of_a_meshed_island(alpha):
+    # Small deviations from the uniform state m = z of the two-layer island, under a uniform field
+    # B0 along the easy axis z, demag off. To first order in w = m_x + i m_y the LLG becomes
+    #   dw/dt = gamma' (i - alpha) A w,  A = diag(B0 + 2 Ku_i / Ms_i) + S,
+    # with S the lumped exchange operator (B_ex = -S m, zero row sums, so the exchange field of
+    # the uniform state vanishes). A is a diagonal scaling of a symmetric matrix, so its
+    # eigenvalues lam are real: each mode precesses at gamma' lam and decays at gamma' alpha lam.
+    # Heun on a linear system is the map w -> (1 + z + z^2/2) w, z = h gamma' (i - alpha) A.
+    m = synth.small_island_mesh()
+    ops = fem.MeshOperators(m.xyz_nm, m.tets, m.tet_region, synth.ecc_materials(), with_demag=False)
+    n, B0 = ops.n, 0.5
+    A = np.diag(B0 + 2.0 * ops.Ku / ops.Ms) + ops.S
+    lam, V = np.linalg.eig(A)
+    assert np.abs(lam.imag).max() == 0.0 and lam.real.min() > B0
+    lam, V = lam.real, V.real
+    p = synth.RunParams(dt_ps=0.1, t_end_ps=5.0, alpha=alpha, rise_ps=0.0, uniform_T=(0.0, 0.0, B0),
+                        term_mask=synth.TERM_EXCHANGE | synth.TERM_ANISOTROPY | synth.TERM_UNIFORM)
+    b = llg.Batch(ops, synth.nominal_islands(1), p)
+    p.substeps = llg.stable_substeps(b)
+    h, steps = p.dt_ps / p.substeps, p.n_intervals * p.substeps
+    gp = llg.GAMMA_PS / (1 + alpha ** 2)
+
+    def start(w):
+        m0 = np.zeros((1, n, 3))
+        m0[0, :, 0], m0[0, :, 1], m0[0, :, 2] = w.real, w.imag, 1.0
+        return m0 / np.linalg.norm(m0, axis=2, keepdims=True)
+
+    # every mode at once, against the discrete linear map: a deviation of 1e-5 leaves
+    # nonlinear terms of relative size 1e-10
+    m0 = start(1e-5 * np.random.default_rng(3).standard_normal(n).astype(complex))
+    w0 = m0[0, :, 0] + 1j * m0[0, :, 1]
+    r = b.run(m0)
+    w = r["m"][0, :, 0] + 1j * r["m"][0, :, 1]
+    z = h * gp * (1j - alpha) * lam
+    w_lin = V @ ((1 + z + z * z / 2) ** steps * np.linalg.solve(V, w0))
+    assert np.abs(w - w_lin).max() < 1e-6 * np.abs(w_lin).max()
+    # the lowest mode alone, against the continuous solution: Heun's phase error per step is
+    # (omega h)^3 / 6, and its amplitude error is of the same order
+    v = V[:, np.argmin(lam)]
+    m0 = start(1e-5 * v / np.abs(v).max() + 0j)
+    r = b.run(m0)
+    w = r["m"][0, :, 0] + 1j * r["m"][0, :, 1]
+    om = gp * lam.min()
+    w_ex = (m0[0, :, 0] + 1j * m0[0, :, 1]) * np.exp((1j - alpha) * om * p.t_end_ps)
+    bound = steps * ((om * h) ** 3 / 6) * math.hypot(1.0, alpha) ** 3
+    assert np.abs(w - w_ex).max() < 2.0 * bound * np.abs(w_ex).max() + 1e-9 * np.abs(w_ex).max()
 
 
 def test_stable_substeps_scales_with_dt(small_ops):
