@@ -2,7 +2,9 @@
 
 Every computation runs in libbpmllg.so; these classes only own handles and
 convert arguments.  Host arrays are numpy; device arrays are torch CUDA
-tensors (or anything with data_ptr()).
+tensors on the context's GPU, contiguous, of the dtype and extents each call
+states (checked here: the library trusts a device pointer with the extents its
+other arguments imply).
 """
 from __future__ import annotations
 
@@ -13,6 +15,26 @@ from ctypes import byref, c_double, c_int32, c_void_p
 import numpy as np
 
 from . import _lib as L
+
+
+def device_tensor(t, device: int, dtype: str, shape, name: str):
+    """Check a tensor whose address goes to the library as a device pointer: a CUDA tensor on
+    the context's device, of torch dtype `dtype` (a name, e.g. "float32"), contiguous, with the
+    given extents (None: any).  Raises ValueError otherwise; returns t."""
+    import torch
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name}: expected a torch CUDA tensor, got {type(t).__name__}")
+    if t.device.index != device:
+        raise ValueError(f"{name}: on cuda:{t.device.index}, the context is on cuda:{device}")
+    if t.dtype != getattr(torch, dtype):
+        raise ValueError(f"{name}: dtype {t.dtype}, expected torch.{dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    got = tuple(int(e) for e in t.shape)
+    if len(got) != len(shape) or any(s is not None and e != int(s) for e, s in zip(got, shape)):
+        want = tuple("*" if s is None else int(s) for s in shape)
+        raise ValueError(f"{name}: shape {got}, expected {want}")
+    return t
 
 
 def run_params(p, precision: int = L.PREC_BF16X3, map_id: int = -1) -> L.bpm_run_params:
@@ -158,7 +180,10 @@ class Context:
         for f, _ in L.bpm_pole_geometry._fields_:
             setattr(g, f, type(getattr(g, f))(geometry.get(f, 0)))
         org = np.ascontiguousarray(origin_nm, np.float32)
+        if org.shape != (3,):
+            raise ValueError(f"origin_nm: {org.shape[0] if org.ndim == 1 else org.shape} values, expected 3")
         if out is not None:
+            device_tensor(out, self.device, "float32", (nz, ny, nx, 3), "out")
             with self.device_order():
                 L.check(self.lib.bpm_head_field_solve(self.h, byref(g), int(nx), int(ny), int(nz), float(h_nm),
                                                       L.ptr(org), L.ptr(out), 1))
@@ -239,6 +264,9 @@ class Context:
         torch's current stream."""
         isl = island_array(islands)
         q = run_params(params, L.PREC_FP32, map_id)
+        device_tensor(m_dev, self.device, "float32", (len(isl), 3, None), "m_dev")
+        if mz_dev is not None:
+            device_tensor(mz_dev, self.device, "float32", (len(isl),), "mz_dev")
         with self.device_order():
             L.check(self.lib.bpm_llg_advance_noalloc(self.h, L.ptr(isl), len(isl), byref(q), int(n_intervals),
                                                      L.ptr(m_dev), int(m_dev.shape[-1]), L.ptr(mz_dev)))
@@ -295,9 +323,23 @@ class Surrogate:
         L.check(self.lib.bpm_surrogate_get_params(self.ctx.h, self.sid, L.ptr(out)))
         return out
 
-    def grad(self, X, Y):
+    def _host_rows(self, X, cols=None, name="X"):
+        """Host rows [N][cols] (cols = n_in by default) as contiguous float32."""
         X = np.ascontiguousarray(X, np.float32)
-        Y = np.ascontiguousarray(Y, np.float32)
+        cols = self.n_in if cols is None else cols
+        if X.ndim != 2 or X.shape[1] != cols:
+            raise ValueError(f"{name}: shape {X.shape}, expected (N, {cols})")
+        return X
+
+    def _host_pairs(self, X, Y):
+        X = self._host_rows(X)
+        Y = self._host_rows(Y, self.n_out, "Y")
+        if Y.shape[0] != X.shape[0]:
+            raise ValueError(f"{X.shape[0]} inputs, {Y.shape[0]} labels")
+        return X, Y
+
+    def grad(self, X, Y):
+        X, Y = self._host_pairs(X, Y)
         g = np.zeros(self.P, np.float32)
         loss = ctypes.c_float()
         L.check(self.lib.bpm_surrogate_grad(self.ctx.h, self.sid, L.ptr(X), L.ptr(Y), X.shape[0], L.ptr(g),
@@ -305,8 +347,7 @@ class Surrogate:
         return g, loss.value
 
     def train(self, X, Y, epochs, batch, lr, weight_decay, beta1=0.9, beta2=0.999, eps=1e-8):
-        X = np.ascontiguousarray(X, np.float32)
-        Y = np.ascontiguousarray(Y, np.float32)
+        X, Y = self._host_pairs(X, Y)
         cfg = L.bpm_train_cfg(int(epochs), int(batch), lr, weight_decay, beta1, beta2, eps, 0)
         steps = int(epochs) * ((X.shape[0] + int(batch) - 1) // int(batch))
         curve = np.zeros(steps, np.float32)
@@ -315,12 +356,13 @@ class Surrogate:
         return curve
 
     def infer(self, X) -> np.ndarray:
-        on_dev = int(hasattr(X, "data_ptr"))
+        on_dev = int(getattr(X, "is_cuda", False))
         if on_dev:
             import torch
+            device_tensor(X, self.ctx.device, "float32", (None, self.n_in), "X")
             P = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
         else:
-            X = np.ascontiguousarray(X, np.float32)
+            X = self._host_rows(X)
             P = np.zeros((X.shape[0], self.n_out), np.float32)
         with self.ctx.device_order() if on_dev else contextlib.nullcontext():
             L.check(self.lib.bpm_surrogate_infer(self.ctx.h, self.sid, L.ptr(X), X.shape[0], L.ptr(P), on_dev))
@@ -334,12 +376,13 @@ class Surrogate:
         n_designs, n_jitter = int(n_designs), int(n_jitter)
         if X.shape[0] != n_designs * n_jitter:
             raise ValueError(f"{X.shape[0]} rows for {n_designs} designs x {n_jitter} jitter samples")
-        on_dev = int(hasattr(X, "data_ptr"))
+        on_dev = int(getattr(X, "is_cuda", False))
         if on_dev:
             import torch
+            device_tensor(X, self.ctx.device, "float32", (n_designs * n_jitter, self.n_in), "X")
             R = torch.empty((n_designs, self.n_out), dtype=torch.float64, device=X.device)
         else:
-            X = np.ascontiguousarray(X, np.float32)
+            X = self._host_rows(X)
             R = np.zeros((n_designs, self.n_out), np.float64)
         with self.ctx.device_order() if on_dev else contextlib.nullcontext():
             L.check(self.lib.bpm_surrogate_screen(self.ctx.h, self.sid, L.ptr(X), n_designs, n_jitter, L.ptr(R),
@@ -382,11 +425,15 @@ class Batch:
         self.destroy()
 
     def set_state(self, m=None, t0_ps: float = 0.0):
-        """m: host numpy [B][3][n] (or a device tensor), None for +z."""
-        on_dev = int(m is not None and hasattr(m, "data_ptr"))
-        ld = self.n if m is None else int(m.shape[-1])
-        if m is not None and not on_dev:
+        """m: host [B][3][ld] float32 (or a CUDA tensor of that shape), None for +z."""
+        on_dev = int(getattr(m, "is_cuda", False))
+        if on_dev:
+            device_tensor(m, self.ctx.device, "float32", (self.B, 3, None), "m")
+        elif m is not None:
             m = np.ascontiguousarray(m, np.float32)
+            if m.ndim != 3 or m.shape[:2] != (self.B, 3):
+                raise ValueError(f"m: shape {m.shape}, expected ({self.B}, 3, ld)")
+        ld = self.n if m is None else int(m.shape[-1])
         with self.ctx.device_order() if on_dev else contextlib.nullcontext():
             L.check(self.lib.bpm_batch_set_state(self.h, L.ptr(m), ld, float(t0_ps), on_dev))
 
@@ -403,7 +450,14 @@ class Batch:
         return dict(m=m, switched=sw.astype(bool), t_sw=tsw, status=st, mz=mz)
 
     def read_device(self, m, switched, t_sw, status, mz):
-        """Stream-ordered read into device tensors (any may be None)."""
+        """Stream-ordered read into device tensors (any may be None): m float32 [B][3][ld],
+        switched uint8 [B], t_sw float32 [B], status int32 [B], mz float32 [B]."""
+        dev, B = self.ctx.device, self.B
+        for t, dt, shape, name in ((m, "float32", (B, 3, None), "m"), (switched, "uint8", (B,), "switched"),
+                                   (t_sw, "float32", (B,), "t_sw"), (status, "int32", (B,), "status"),
+                                   (mz, "float32", (B,), "mz")):
+            if t is not None:
+                device_tensor(t, dev, dt, shape, name)
         ld = self.n if m is None else int(m.shape[-1])
         with self.ctx.device_order():
             L.check(self.lib.bpm_batch_read(self.h, L.ptr(m), ld, L.ptr(switched), L.ptr(t_sw), L.ptr(status),
