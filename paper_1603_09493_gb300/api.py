@@ -133,6 +133,10 @@ class Context:
         tets = np.ascontiguousarray(mesh.tets, np.int32)
         reg = np.ascontiguousarray(mesh.tet_region, np.int32)
         mats = np.asarray(mats, np.float64)
+        if xyz.ndim != 2 or xyz.shape[1] != 3 or tets.ndim != 2 or tets.shape[1] != 4 or \
+                reg.shape != (tets.shape[0],) or mats.ndim != 2:
+            raise ValueError(f"mesh: xyz {xyz.shape} (n, 3), tets {tets.shape} (m, 4), regions {reg.shape} (m,), "
+                             f"materials {mats.shape} (regions, fields)")
         cm = (L.bpm_region_mat * len(mats))(*[L.bpm_region_mat(*map(float, r)) for r in mats])
         mid = c_int32()
         L.check(self.lib.bpm_mesh_upload(self.h, L.ptr(xyz), xyz.shape[0], L.ptr(tets), tets.shape[0],
@@ -164,8 +168,10 @@ class Context:
 
     def headmap_upload(self, hm) -> int:
         B = np.ascontiguousarray(hm.B_T, np.float32)
-        nz, ny, nx = B.shape[:3]
         org = np.ascontiguousarray(hm.origin_nm, np.float32)
+        if B.ndim != 4 or B.shape[3] != 3 or org.shape != (3,):
+            raise ValueError(f"head map: B_T {B.shape}, expected (nz, ny, nx, 3); origin {org.shape}, expected (3,)")
+        nz, ny, nx = B.shape[:3]
         mid = c_int32()
         L.check(self.lib.bpm_headmap_upload(self.h, L.ptr(B), nx, ny, nz, float(hm.h_nm), L.ptr(org),
                                             byref(mid)))

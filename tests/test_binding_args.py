@@ -105,3 +105,20 @@ def test_context_outputs_are_checked_before_the_library():
         ctx.llg_advance_noalloc(isl, synth.RunParams(), 1, _Dev((3, 3, 10)))
     with pytest.raises(ValueError, match="mz_dev"):
         ctx.llg_advance_noalloc(isl, synth.RunParams(), 1, _Dev((4, 3, 10)), _Dev((4,), torch.float64))
+
+
+def test_uploads_are_checked_before_the_library():
+    ctx = object.__new__(api.Context)
+    ctx.lib, ctx.h, ctx.device = _NoLib(), None, 0
+    hm = synth.synthetic_head_map(nx=8, ny=8, nz=4)
+    with pytest.raises(ValueError, match="head map"):
+        ctx.headmap_upload(synth.HeadMap(B_T=hm.B_T[..., 0], origin_nm=hm.origin_nm, h_nm=hm.h_nm))
+    with pytest.raises(ValueError, match="head map"):
+        ctx.headmap_upload(synth.HeadMap(B_T=hm.B_T, origin_nm=hm.origin_nm[:2], h_nm=hm.h_nm))
+    mesh = synth.small_island_mesh()
+    bad = types.SimpleNamespace(xyz_nm=mesh.xyz_nm.T, tets=mesh.tets, tet_region=mesh.tet_region)
+    with pytest.raises(ValueError, match="mesh"):
+        ctx.mesh_upload(bad, synth.ecc_materials())
+    bad = types.SimpleNamespace(xyz_nm=mesh.xyz_nm, tets=mesh.tets, tet_region=mesh.tet_region[:-1])
+    with pytest.raises(ValueError, match="mesh"):
+        ctx.mesh_upload(bad, synth.ecc_materials())
