@@ -314,7 +314,11 @@ class Surrogate:
         self.ctx, self.lib = ctx, ctx.lib
         self.n_in, self.n_out = n_in, n_out
         cfg = L.bpm_mlp_cfg(n_in, width, depth, n_out)
-        flat = np.ascontiguousarray(params, np.float32)
+        flat = np.ascontiguousarray(params, np.float32).reshape(-1)
+        widths = [int(n_in)] + [int(width)] * int(depth) + [int(n_out)]
+        count = sum(a * b + b for a, b in zip(widths[:-1], widths[1:]))   # W [out][in], then b, per layer
+        if flat.size != count:
+            raise ValueError(f"expected {count} parameters for sizes {tuple(sizes)}, got {flat.size}")
         sid = c_int32()
         L.check(self.lib.bpm_surrogate_create(ctx.h, byref(cfg), L.ptr(flat), byref(sid)))
         self.sid = sid.value

@@ -122,3 +122,13 @@ def test_uploads_are_checked_before_the_library():
     bad = types.SimpleNamespace(xyz_nm=mesh.xyz_nm, tets=mesh.tets, tet_region=mesh.tet_region[:-1])
     with pytest.raises(ValueError, match="mesh"):
         ctx.mesh_upload(bad, synth.ecc_materials())
+
+
+def test_surrogate_parameter_count_is_checked_before_the_library():
+    ctx = types.SimpleNamespace(lib=_NoLib(), h=None, device=0)
+    sizes = [16, 64, 64, 2]
+    flat = synth.mlp_init_params(sizes, seed=1)
+    with pytest.raises(ValueError, match="parameters"):
+        api.Surrogate(ctx, (16, 64, 2, 2), flat[:-1])
+    with pytest.raises(AssertionError, match="library called"):      # the right count reaches it
+        api.Surrogate(ctx, (16, 64, 2, 2), flat)
