@@ -292,6 +292,8 @@ class Context:
         E = np.zeros((D, n_images), np.float64)
         EB = np.zeros(D, np.float64)
         mi = None if m_init is None else np.ascontiguousarray(m_init, np.float32)
+        if mi is not None and mi.shape != (D, int(n_images), 3, n):
+            raise ValueError(f"m_init: shape {mi.shape}, expected ({D}, {int(n_images)}, 3, {n})")
         mp = np.zeros((D, n_images, 3, n), np.float32) if want_path else None
         it = c_int32()
         fm = c_double()

@@ -132,3 +132,20 @@ def test_surrogate_parameter_count_is_checked_before_the_library():
         api.Surrogate(ctx, (16, 64, 2, 2), flat[:-1])
     with pytest.raises(AssertionError, match="library called"):      # the right count reaches it
         api.Surrogate(ctx, (16, 64, 2, 2), flat)
+
+
+def test_band_start_is_checked_before_the_band_runs():
+    calls = []
+
+    class _InfoLib(_NoLib):
+        def bpm_mesh_info_get(self, h, mid, info):
+            calls.append("info")
+            info._obj.n_nodes = 10
+            return 0
+
+    ctx = object.__new__(api.Context)
+    ctx.lib, ctx.h, ctx.device = _InfoLib(), None, 0
+    isl = synth.nominal_islands(2)
+    with pytest.raises(ValueError, match="m_init"):
+        ctx.neb(isl, 5, 10, 0.1, 1.0, m_init=np.zeros((2, 5, 10, 3), np.float32))
+    assert calls == ["info"]
